@@ -1,0 +1,170 @@
+/*
+ * chordal.h — C ABI of libchordal.so, the GB300 (sm_103a) parallel chordality
+ * test of "A Parallel Algorithm to Test Chordality of Graphs" (arXiv:1508.06329).
+ *
+ * The test has two parts (Section 6): a LexBFS order computed by partition
+ * refinement (Sections 4.2 and 6.1), then the perfect-elimination check of
+ * that order (Sections 5.3 and 6.2).  G is chordal iff the LexBFS order is a
+ * perfect elimination order (Theorem 5.1).
+ *
+ * Conventions used by every entry point
+ *   - Vertex ids are 0-based, 0..n-1.
+ *   - Dense graphs: `rows` holds n rows of `words_per_row` uint32 words; bit
+ *     (j & 31) of rows[i * words_per_row + (j >> 5)] is 1 iff ij is an edge
+ *     (LSB first).  The matrix must be symmetric with a zero diagonal and zero
+ *     padding bits; words_per_row >= ceil(n / 32).
+ *   - CSR graphs: row_ptr int64[n + 1], col int32[nnz]; each row sorted
+ *     ascending, no self-loops, no duplicates, symmetric.
+ *   - order int32[n]: order[i] is the i-th visited vertex (the ordering π of
+ *     Section 3.1); pos int32[n] is its inverse π^{-1}.
+ *   - Tie-break: among the unnumbered vertices whose label is
+ *     lexicographically largest, the lowest id is visited first (the paper
+ *     leaves the choice open, Section 6.1; this fixes one LexBFS order).
+ *   - Witness: when the graph is not chordal, v is the vertex with the
+ *     smallest order index whose earlier neighbourhood LN_v is not a clique
+ *     (the "first such node" of Section 5.4), p = p(v) is its neighbour with
+ *     the largest order index below v's, and u is the smallest id in
+ *     (LN_v - {p}) \ N(p).  When chordal, v = p = u = -1.
+ *   - Pointers named "device" are CUDA device pointers owned by the caller;
+ *     the library never frees them.  Calls are asynchronous on `stream`
+ *     unless the name ends in _host; results are valid after the stream is
+ *     synchronised.  The library allocates only its own workspace, held by the
+ *     context and grown on demand (device memory, plus pinned host staging).
+ *   - Every call returns a cg_status.  On CG_ECUDA / CG_EINVAL,
+ *     cg_last_error_string() describes the failure (thread-local).
+ *   - A context may be used by one host thread at a time.
+ */
+#ifndef CHORDAL_GB300_H
+#define CHORDAL_GB300_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CG_OK = 0,
+    CG_EINVAL = 1,    /* bad size, layout or pointer */
+    CG_ENOMEM = 2,    /* workspace allocation failed */
+    CG_ECUDA = 3,     /* a CUDA call or kernel launch failed */
+    CG_ETIMEOUT = 4,  /* a bounded wait (queue drain) expired */
+    CG_EAGAIN = 5,    /* queue full / result not ready yet */
+} cg_status;
+
+/* Dense bit-packed graph (device memory). */
+typedef struct {
+    int32_t n;
+    int32_t words_per_row;
+    const uint32_t *rows;
+} cg_dense;
+
+/* CSR graph (device memory). */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int64_t *row_ptr;
+    const int32_t *col;
+} cg_csr;
+
+/* Verdict and witness (see conventions). */
+typedef struct {
+    int32_t chordal;
+    int32_t v, p, u;
+} cg_result;
+
+typedef struct {
+    int32_t device;          /* CUDA device ordinal the context works on */
+    int32_t validate;        /* 1: check sizes and CSR sortedness on entry (costs a sync) */
+    int32_t threads_override;/* 0: autotuned CTA size for the LexBFS kernels; else 128..1024 */
+    int32_t reserved;
+} cg_config;
+
+typedef struct cg_context cg_context;
+
+/* Library version, e.g. "chordal-gb300 0.1.0 (sm_103a)". */
+const char *cg_version(void);
+/* Last error message of the calling thread ("" if none). */
+const char *cg_last_error_string(void);
+
+/* Create / destroy a context.  cfg may be NULL (device 0, defaults).  The
+ * context owns device workspace and pinned staging memory; destroy frees it
+ * (synchronising the device first). */
+int cg_context_create(const cg_config *cfg, cg_context **out);
+int cg_context_destroy(cg_context *ctx);
+
+/*
+ * LexBFS order of a dense graph (Section 4.2: pick the first vertex of the
+ * first class, split every class C into C ∩ N_x placed before C \ N_x;
+ * Section 6.1 runs it on the GPU).  One persistent CTA walks all n steps with
+ * the partition state in shared memory (n <= 16384) or in the workspace.
+ *   g      device graph, n >= 0, n <= 131072
+ *   order  device int32[n] (written)
+ *   pos    device int32[n] (written) or NULL
+ */
+int cg_lexbfs_order_dense(cg_context *ctx, const cg_dense *g, int32_t *order, int32_t *pos,
+                          cudaStream_t stream);
+
+/*
+ * Perfect-elimination check of a caller-given order (Sections 5.3 and 6.2):
+ * p(v) = the neighbour of v with the largest order index below v's, then
+ * LN_v - {p(v)} ⊆ N(p(v)) for every v.  The order need not be a LexBFS
+ * order; for a LexBFS order the verdict is the chordality verdict.
+ *   order   device int32[n], a permutation of 0..n-1 (not checked unless
+ *           cfg.validate)
+ *   parent  device int32[n] (written: p(v) or -1) or NULL
+ *   res     device cg_result (written)
+ */
+int cg_peo_check_dense(cg_context *ctx, const cg_dense *g, const int32_t *order, int32_t *parent,
+                       cg_result *res, cudaStream_t stream);
+
+/* The whole test on one dense graph: LexBFS, then the check.
+ *   res    device cg_result (written)
+ *   order  device int32[n] (written) or NULL */
+int cg_chordal_test_dense(cg_context *ctx, const cg_dense *g, cg_result *res, int32_t *order,
+                          cudaStream_t stream);
+
+/* The same test with HOST buffers: copies rows (n * words_per_row uint32,
+ * preferably pinned) to the device, runs, copies the result (and the order
+ * when host_order != NULL) back and synchronises the stream. */
+int cg_chordal_test_dense_host(cg_context *ctx, int32_t n, int32_t words_per_row,
+                               const uint32_t *host_rows, cg_result *host_res, int32_t *host_order,
+                               cudaStream_t stream);
+
+/*
+ * Many dense graphs in one pass (the batching of independent tests): each
+ * graph's LexBFS runs in its own CTA of one persistent launch, graphs handed
+ * out largest first; the checks of all graphs share one grid.
+ *   graphs         HOST array of `count` descriptors whose `rows` are device
+ *                  pointers
+ *   res            device cg_result[count] (written)
+ *   orders         device int32[sum n] (written, graph k at order_offsets[k])
+ *                  or NULL
+ *   order_offsets  HOST int64[count] or NULL (then graphs are packed in
+ *                  input order)
+ */
+int cg_chordal_test_batch(cg_context *ctx, const cg_dense *graphs, int32_t count, cg_result *res,
+                          int32_t *orders, const int64_t *order_offsets, cudaStream_t stream);
+
+/*
+ * Per-phase timing (tracing aid; not part of the paper).  When enabled, each
+ * call records CUDA events on its stream around the LexBFS launch and around
+ * the check (check + finalize launches).  cg_profile_read waits for the
+ * recorded events, returns the sums since the last read and resets them.
+ */
+typedef struct {
+    double lexbfs_ms;        /* summed LexBFS kernel time */
+    double check_ms;         /* summed perfect-elimination check time */
+    int64_t lexbfs_launches;
+    int64_t check_launches;
+    int64_t kernel_launches; /* all kernels this library launched since the last read */
+} cg_profile;
+
+int cg_profile_enable(cg_context *ctx, int enable);
+int cg_profile_read(cg_context *ctx, cg_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHORDAL_GB300_H */

@@ -1,0 +1,218 @@
+"""ctypes binding of libchordal.so (argument marshalling only).
+
+Every C entry point of ``include/chordal.h`` is exposed under the same name
+with the same arguments (device pointers as ints, ``cudaStream_t`` as an int
+handle).  The helpers at the bottom accept torch tensors and pass their data
+pointers and the current torch stream; all work runs in the library's CUDA
+kernels.  There is no fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libchordal.so")
+
+CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ETIMEOUT, CG_EAGAIN = range(6)
+_STATUS = {0: "CG_OK", 1: "CG_EINVAL", 2: "CG_ENOMEM", 3: "CG_ECUDA", 4: "CG_ETIMEOUT", 5: "CG_EAGAIN"}
+
+
+class ChordalError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class cg_dense(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("words_per_row", ctypes.c_int32), ("rows", ctypes.c_void_p)]
+
+
+class cg_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p)]
+
+
+class cg_result(ctypes.Structure):
+    _fields_ = [("chordal", ctypes.c_int32), ("v", ctypes.c_int32), ("p", ctypes.c_int32), ("u", ctypes.c_int32)]
+
+    def astuple(self):
+        return (self.chordal, self.v, self.p, self.u)
+
+
+class cg_profile(ctypes.Structure):
+    _fields_ = [("lexbfs_ms", ctypes.c_double), ("check_ms", ctypes.c_double), ("lexbfs_launches", ctypes.c_int64),
+                ("check_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+
+
+class cg_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("validate", ctypes.c_int32), ("threads_override", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+
+# name -> argtypes (restype int unless noted)
+SIGNATURES = {
+    "cg_version": ([], ctypes.c_char_p),
+    "cg_last_error_string": ([], ctypes.c_char_p),
+    "cg_context_create": ([P, P], ctypes.c_int),
+    "cg_context_destroy": ([P], ctypes.c_int),
+    "cg_lexbfs_order_dense": ([P, P, P, P, P], ctypes.c_int),
+    "cg_peo_check_dense": ([P, P, P, P, P, P], ctypes.c_int),
+    "cg_chordal_test_dense": ([P, P, P, P, P], ctypes.c_int),
+    "cg_chordal_test_dense_host": ([P, I32, I32, P, P, P, P], ctypes.c_int),
+    "cg_chordal_test_batch": ([P, P, I32, P, P, P, P], ctypes.c_int),
+    "cg_profile_enable": ([P, I32], ctypes.c_int),
+    "cg_profile_read": ([P, P], ctypes.c_int),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libchordal.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise ImportError(f"{p} is missing: build it with `python -m paper_1508_06329_gb300.build` "
+                                  "(there is no CPU fallback)")
+            lib = ctypes.CDLL(p)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != CG_OK:
+        raise ChordalError(status, load().cg_last_error_string().decode())
+
+
+def _fn(name):
+    def call(*args):
+        return getattr(load(), name)(*args)
+    call.__name__ = name
+    return call
+
+
+# Same names as the C ABI: raw calls returning the status code.
+cg_version = _fn("cg_version")
+cg_last_error_string = _fn("cg_last_error_string")
+cg_context_create = _fn("cg_context_create")
+cg_context_destroy = _fn("cg_context_destroy")
+cg_lexbfs_order_dense = _fn("cg_lexbfs_order_dense")
+cg_peo_check_dense = _fn("cg_peo_check_dense")
+cg_chordal_test_dense = _fn("cg_chordal_test_dense")
+cg_chordal_test_dense_host = _fn("cg_chordal_test_dense_host")
+cg_chordal_test_batch = _fn("cg_chordal_test_batch")
+cg_profile_enable = _fn("cg_profile_enable")
+cg_profile_read = _fn("cg_profile_read")
+
+
+# --------------------------------------------------------------------------- torch-facing helpers
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Context:
+    """Owns a cg_context (device workspace + pinned staging)."""
+
+    def __init__(self, device: int = 0, threads_override: int = 0, validate: int = 0):
+        cfg = cg_config(device, validate, threads_override, 0)
+        h = ctypes.c_void_p()
+        _check(cg_context_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def profile(self, enable: bool = True):
+        _check(cg_profile_enable(self.handle, 1 if enable else 0))
+
+    def read_profile(self) -> dict:
+        p = cg_profile()
+        _check(cg_profile_read(self.handle, ctypes.byref(p)))
+        return {f: getattr(p, f) for f, _ in cg_profile._fields_}
+
+    def close(self):
+        if self.handle:
+            _check(cg_context_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dense_desc(rows, n: int) -> cg_dense:
+    """rows: CUDA tensor of 32-bit words, shape [n, words] (int32 or uint32)."""
+    words = int(rows.shape[1]) if rows.dim() == 2 else 0
+    if rows.element_size() != 4 or not rows.is_contiguous():
+        raise ValueError("rows must be a contiguous tensor of 32-bit words")
+    return cg_dense(n, words, _ptr(rows))
+
+
+def lexbfs_order_dense(ctx: Context, rows, n: int, order, pos=None, stream=None):
+    d = dense_desc(rows, n)
+    _check(cg_lexbfs_order_dense(ctx.handle, ctypes.byref(d), _ptr(order), _ptr(pos), _stream(stream)))
+
+
+def chordal_test_dense(ctx: Context, rows, n: int, res, order=None, stream=None):
+    """res: CUDA int32 tensor [4] -> (chordal, v, p, u)."""
+    d = dense_desc(rows, n)
+    _check(cg_chordal_test_dense(ctx.handle, ctypes.byref(d), _ptr(res), _ptr(order), _stream(stream)))
+
+
+def peo_check_dense(ctx: Context, rows, n: int, order, res, parent=None, stream=None):
+    d = dense_desc(rows, n)
+    _check(cg_peo_check_dense(ctx.handle, ctypes.byref(d), _ptr(order), _ptr(parent), _ptr(res), _stream(stream)))
+
+
+def chordal_test_dense_host(ctx: Context, rows_host, n: int, order_host=None, stream=None) -> tuple:
+    """rows_host: CPU tensor/ndarray of 32-bit words [n, words] (pinned preferred)."""
+    import numpy as np
+    if hasattr(rows_host, "data_ptr"):
+        ptr, words = int(rows_host.data_ptr()), int(rows_host.shape[1]) if rows_host.dim() == 2 else 0
+        optr = 0 if order_host is None else int(order_host.data_ptr())
+    else:
+        a = np.ascontiguousarray(rows_host)
+        ptr, words = a.ctypes.data, (a.shape[1] if a.ndim == 2 else 0)
+        optr = 0 if order_host is None else order_host.ctypes.data
+    out = cg_result()
+    _check(cg_chordal_test_dense_host(ctx.handle, n, words, ptr, ctypes.byref(out), optr, _stream(stream)))
+    return out.astuple()
+
+
+def chordal_test_batch(ctx: Context, graphs, res, orders=None, order_offsets=None, stream=None):
+    """graphs: list of (rows_tensor, n); res: CUDA int32 tensor [count, 4]."""
+    count = len(graphs)
+    arr = (cg_dense * max(count, 1))()
+    for k, (rows, n) in enumerate(graphs):
+        arr[k] = dense_desc(rows, n)
+    offs = None
+    if order_offsets is not None:
+        offs = (ctypes.c_int64 * max(count, 1))(*[int(x) for x in order_offsets])
+    _check(cg_chordal_test_batch(ctx.handle, arr, count, _ptr(res), _ptr(orders),
+                                 offs if offs is not None else None, _stream(stream)))

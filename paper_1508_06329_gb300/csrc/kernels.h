@@ -1,0 +1,43 @@
+// kernels.h — host-side launchers shared between the libchordal sources.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace cg {
+
+// ---- dense LexBFS (lexbfs_dense.cu)
+struct LexPlan {
+    int threads;        // CTA size
+    bool rows_smem;     // adjacency copied into shared memory
+    bool wide_ids;      // 32-bit ids, state in a global workspace
+    size_t smem_bytes;  // dynamic shared memory per CTA
+    size_t gstate_bytes;// global state bytes per CTA (wide ids only)
+};
+
+// Picks the kernel variant for graphs of at most n_max vertices.
+// threads_override = 0 lets the size rule decide.
+int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan);
+
+// Runs LexBFS for `count` graphs, one CTA each (grid = min(count, ctas)).
+// descs: device array, or nullptr to use `single` (count must be 1).
+// work_counter: device int, zeroed by the launcher (dynamic graph hand-out).
+int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
+                        int32_t *order, int32_t *pos, void *gstate, int *work_counter, cudaStream_t stream);
+
+// ---- dense perfect-elimination check (peo_dense.cu)
+// keys: device u64[count], set to ~0 by the launcher.
+int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
+                     const int32_t *order, const int32_t *pos, int32_t *parent, unsigned long long *keys,
+                     int num_sms, cudaStream_t stream);
+
+// pos[order[i]] = i for every graph (order values outside 0..n-1 are skipped).
+int invert_order_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
+                        const int32_t *order, int32_t *pos, int num_sms, cudaStream_t stream);
+
+int finalize_launch(const DenseDesc *descs, DenseDesc single, int count, const unsigned long long *keys,
+                    const int32_t *order, const int32_t *parent, cg_result *res, cudaStream_t stream);
+
+}  // namespace cg

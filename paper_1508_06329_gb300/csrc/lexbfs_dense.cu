@@ -1,0 +1,138 @@
+// lexbfs_dense.cu — kernels and launcher of the one-CTA-per-graph dense LexBFS.
+#include <algorithm>
+
+#include "kernels.h"
+#include "lexbfs_dense.cuh"
+
+namespace cg {
+
+namespace {
+
+constexpr size_t kSmemLimit = 227 * 1024;   // opt-in dynamic shared memory per CTA (sm_100 family)
+constexpr int kSmemMaxN = 16384;             // 16-bit ids
+constexpr int kWideMaxN = 131072;            // 32-bit ids: 4 words per thread at 1024 threads
+
+template <typename Id, int T, int WPT, bool ROWS_SMEM>
+__global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
+                                                         int count, int32_t *__restrict__ order,
+                                                         int32_t *__restrict__ pos, unsigned char *gstate,
+                                                         size_t gstate_stride, int *work_counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    LexScalars *sc = reinterpret_cast<LexScalars *>(smem);
+    unsigned char *free_smem = smem + kLexScalarBytes;
+    for (;;) {
+        if (threadIdx.x == 0) sc->next_graph = count == 1 ? (int)blockIdx.x : atomicAdd(work_counter, 1);
+        __syncthreads();
+        const int gi = sc->next_graph;
+        __syncthreads();
+        if (gi >= count) break;
+        const DenseDesc d = descs ? descs[gi] : single;
+        const int n = d.n;
+        LexState<Id> st;
+        unsigned char *p = free_smem;
+        if (gstate) {
+            st = lex_state_carve<Id>(gstate + (size_t)blockIdx.x * gstate_stride, n);
+        } else {
+            st = lex_state_carve<Id>(p, n);
+            p += lex_state_bytes<Id>(n);
+        }
+        const uint32_t *rows = d.rows;
+        int stride = d.words;
+        if (ROWS_SMEM) {
+            const int wn = (n + 31) >> 5;
+            uint32_t *srows = reinterpret_cast<uint32_t *>(p);
+            const int64_t total = (int64_t)n * wn;
+            for (int64_t k = threadIdx.x; k < total; k += T) {
+                const int r = (int)(k / wn), w = (int)(k - (int64_t)r * wn);
+                srows[k] = __ldg(d.rows + (size_t)r * d.words + w);
+            }
+            rows = srows;
+            stride = wn;
+            __syncthreads();
+        }
+        lexbfs_cta<Id, T, WPT>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr);
+        __syncthreads();
+        if (count == 1) break;
+    }
+}
+
+template <typename Id, int T, int WPT, bool ROWS_SMEM>
+int launch_variant(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
+                   int32_t *order, int32_t *pos, void *gstate, int *work_counter, cudaStream_t stream) {
+    auto kern = lexbfs_dense_kernel<Id, T, WPT, ROWS_SMEM>;
+    CG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes));
+    if (count > 1) CG_CUDA_TRY(cudaMemsetAsync(work_counter, 0, sizeof(int), stream));
+    kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, single, count, order, pos,
+                                               static_cast<unsigned char *>(gstate), plan.gstate_bytes,
+                                               work_counter);
+    CG_LAUNCH_CHECK("lexbfs_dense_kernel");
+    return CG_OK;
+}
+
+}  // namespace
+
+int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
+    if (n_max < 0 || n_max > kWideMaxN)
+        return set_error(CG_EINVAL, "dense LexBFS supports n <= %d (got %d); use the CSR entry points", kWideMaxN,
+                         n_max);
+    LexPlan p{};
+    const int n = std::max(n_max, 1);
+    const int wn = (n + 31) / 32;
+    if (n <= kSmemMaxN) {
+        const size_t state = lex_state_bytes<uint16_t>(n);
+        const size_t rows = (size_t)n * wn * 4;
+        p.wide_ids = false;
+        p.rows_smem = kLexScalarBytes + state + rows <= kSmemLimit;
+        int th = n <= 512 ? 128 : (n <= 2048 ? 256 : 512);
+        if (threads_override) th = threads_override;
+        // words per thread must cover the row
+        while ((int64_t)th * (th == 128 ? 4 : th == 256 ? 2 : 1) < wn) th *= 2;
+        p.threads = std::min(th, 1024);
+        p.smem_bytes = kLexScalarBytes + state + (p.rows_smem ? rows : 0);
+        p.gstate_bytes = 0;
+    } else {
+        p.wide_ids = true;
+        p.rows_smem = false;
+        p.threads = 1024;
+        p.smem_bytes = kLexScalarBytes;
+        p.gstate_bytes = (lex_state_bytes<uint32_t>(n) + 255) & ~size_t(255);
+    }
+    if (p.threads != 128 && p.threads != 256 && p.threads != 512 && p.threads != 1024)
+        return set_error(CG_EINVAL, "unsupported CTA size %d", p.threads);
+    *plan = p;
+    return CG_OK;
+}
+
+int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
+                        int32_t *order, int32_t *pos, void *gstate, int *work_counter, cudaStream_t stream) {
+    if (count <= 0) return CG_OK;
+    ctas = std::max(1, std::min(ctas, count));
+    if (plan.wide_ids)
+        return launch_variant<uint32_t, 1024, 4, false>(plan, descs, single, count, ctas, order, pos, gstate,
+                                                         work_counter, stream);
+    switch (plan.threads) {
+        case 128:
+            return plan.rows_smem ? launch_variant<uint16_t, 128, 4, true>(plan, descs, single, count, ctas, order,
+                                                                           pos, nullptr, work_counter, stream)
+                                  : launch_variant<uint16_t, 128, 4, false>(plan, descs, single, count, ctas,
+                                                                            order, pos, nullptr, work_counter,
+                                                                            stream);
+        case 256:
+            return plan.rows_smem ? launch_variant<uint16_t, 256, 2, true>(plan, descs, single, count, ctas, order,
+                                                                           pos, nullptr, work_counter, stream)
+                                  : launch_variant<uint16_t, 256, 2, false>(plan, descs, single, count, ctas,
+                                                                            order, pos, nullptr, work_counter,
+                                                                            stream);
+        case 512:
+            return plan.rows_smem ? launch_variant<uint16_t, 512, 1, true>(plan, descs, single, count, ctas, order,
+                                                                           pos, nullptr, work_counter, stream)
+                                  : launch_variant<uint16_t, 512, 1, false>(plan, descs, single, count, ctas,
+                                                                            order, pos, nullptr, work_counter,
+                                                                            stream);
+        default:
+            return launch_variant<uint16_t, 1024, 1, false>(plan, descs, single, count, ctas, order, pos, nullptr,
+                                                            work_counter, stream);
+    }
+}
+
+}  // namespace cg

@@ -1,0 +1,297 @@
+// lexbfs_dense.cuh — LexBFS by partition refinement, one CTA per graph.
+//
+// Method (Section 4.2 of the paper; its GPU form in Section 6.1): the
+// unnumbered vertices are partitioned into classes ordered top first.  Each
+// step visits the first vertex x of the first class, then replaces every
+// class C by C ∩ N_x followed by C \ N_x (Observation 6.1: the new class goes
+// right before the class it came from).  Within a class vertices are kept in
+// id order, so the visited vertex is the lowest id of the top class.
+//
+// GPU form used here (differs from the paper's four kernels per step, whose
+// racy pick and racy set creation are replaced by deterministic rules):
+//   * state: cls[v] (class id per vertex), a doubly linked class list with a
+//     head sentinel, and per class one word packing (size, moved-this-step);
+//     everything sits in shared memory for n <= 16384 (16-bit ids), otherwise
+//     in a global workspace (32-bit ids);
+//   * the pivot row is read word-parallel (thread t owns words t, t+T, ...);
+//     each unnumbered neighbour y bumps the moved count of its class with a
+//     shared-memory atomic; the first arrival per class is its allocator;
+//   * allocators split a class only when it loses some but not all members
+//     (C ∩ N_x and C \ N_x both non-empty), taking a fresh id from a free
+//     stack and linking it right before C;  a class that moves entirely keeps
+//     its id and place;
+//   * the relabel cls[y] = child[cls[y]] of a step's moved vertices is
+//     deferred to the next step and done by the thread owning y's word;
+//   * the next pivot is the lowest moved vertex of the top class (an atomicMin
+//     collected while splitting), or of the class after it when the top class
+//     empties; only when neither class lost members is a class scan needed.
+//     A known pivot's row is requested right after the first barrier, so its
+//     load overlaps the list update.  Two __syncthreads per step.
+#pragma once
+#include "common.cuh"
+
+namespace cg {
+
+template <typename Id>
+struct IdTraits;
+template <>
+struct IdTraits<uint16_t> {
+    using Sz = uint32_t;
+    static constexpr int kShift = 16;
+    static constexpr uint32_t kMask = 0xFFFFu;
+};
+template <>
+struct IdTraits<uint32_t> {
+    using Sz = unsigned long long;
+    static constexpr int kShift = 32;
+    static constexpr unsigned long long kMask = 0xFFFFFFFFull;
+};
+
+template <typename Id>
+struct LexState {
+    typename IdTraits<Id>::Sz *sz;  // [n]     size | moved-this-step << kShift
+    Id *cls;                        // [n]     class of each vertex, kNumbered once visited
+    Id *child;                      // [n]     class receiving a class's pivot neighbours
+    Id *freel;                      // [n]     stack of unused class ids
+    Id *cnext;                      // [n + 1] class list; index n is the head sentinel
+    Id *cprev;                      // [n + 1]
+};
+
+struct LexScalars {
+    int free_top;
+    int next_graph;
+    unsigned front_min[2];
+    unsigned second_min[2];
+    unsigned red[32];
+};
+
+constexpr unsigned kNoVertex = 0xFFFFFFFFu;
+
+template <typename Id>
+__host__ __device__ inline size_t lex_state_bytes(int n) {
+    using Sz = typename IdTraits<Id>::Sz;
+    size_t b = (size_t)n * sizeof(Sz) + (size_t)n * sizeof(Id) * 3 + (size_t)(n + 1) * sizeof(Id) * 2;
+    return (b + 15) & ~size_t(15);
+}
+
+template <typename Id>
+__device__ inline LexState<Id> lex_state_carve(unsigned char *base, int n) {
+    using Sz = typename IdTraits<Id>::Sz;
+    LexState<Id> s;
+    s.sz = reinterpret_cast<Sz *>(base);
+    Id *p = reinterpret_cast<Id *>(base + (size_t)n * sizeof(Sz));
+    s.cls = p;
+    s.child = p + n;
+    s.freel = p + 2 * (size_t)n;
+    s.cnext = p + 3 * (size_t)n;
+    s.cprev = p + 4 * (size_t)n + 1;
+    return s;
+}
+
+constexpr size_t kLexScalarBytes = (sizeof(LexScalars) + 15) & ~size_t(15);
+
+// Word w of row x, padding bits cleared.
+__device__ __forceinline__ uint32_t row_word(const uint32_t *__restrict__ rows, int stride, int x, int w,
+                                             int wn, uint32_t lastmask) {
+    uint32_t v = rows[(size_t)x * stride + w];
+    return w == wn - 1 ? (v & lastmask) : v;
+}
+
+// One CTA computes the LexBFS order of one graph.  rows/stride address the
+// adjacency (global memory, or a compact shared-memory copy).
+template <typename Id, int T, int WPT>
+__device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n, LexState<Id> st,
+                           LexScalars *sc, int32_t *__restrict__ order, int32_t *__restrict__ pos) {
+    using Tr = IdTraits<Id>;
+    using Sz = typename Tr::Sz;
+    const Id kNumbered = (Id)~(Id)0;
+    const Id kNone = (Id)(kNumbered - 1);
+    const int t = threadIdx.x;
+    if (n <= 0) return;
+    const Id HEAD = (Id)n;
+    const int wn = (n + 31) >> 5;
+    const uint32_t lastmask = (n & 31) ? ((1u << (n & 31)) - 1u) : 0xFFFFFFFFu;
+
+    for (int v = t; v < n; v += T) st.cls[v] = 0;
+    for (int k = t; k < n - 1; k += T) st.freel[k] = (Id)(k + 1);
+    if (t == 0) {
+        st.sz[0] = (Sz)n;
+        st.cnext[HEAD] = 0;
+        st.cprev[0] = HEAD;
+        st.cnext[0] = kNone;
+        sc->free_top = n - 1;
+        sc->front_min[0] = sc->front_min[1] = kNoVertex;
+        sc->second_min[0] = sc->second_min[1] = kNoVertex;
+    }
+    uint32_t row_cur[WPT], row_prev[WPT], row_nxt[WPT], amask[WPT];
+    int x = 0;
+#pragma unroll
+    for (int k = 0; k < WPT; ++k) {
+        const int w = k * T + t;
+        row_cur[k] = w < wn ? row_word(rows, stride, x, w, wn, lastmask) : 0u;
+        row_prev[k] = 0u;
+        row_nxt[k] = 0u;
+        amask[k] = 0u;
+    }
+    Id pending_free = kNone;
+    __syncthreads();
+
+    for (int i = 0; i < n; ++i) {
+        const int slot = i & 1;
+        const Id f = st.cnext[HEAD];
+        const Id g = st.cnext[f];
+        const Sz fsz = st.sz[f] & Tr::kMask;  // still counts x
+
+        // ---- phase S: deferred relabel, number x, split by N(x)
+        if (t == 0) {
+            if (pending_free != kNone) {
+                st.freel[sc->free_top] = pending_free;
+                sc->free_top += 1;
+                pending_free = kNone;
+            }
+            order[i] = x;
+            if (pos) pos[x] = i;
+        }
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+            const int w = k * T + t;
+            uint32_t am = 0u;
+            if (w < wn) {
+                uint32_t bits = row_prev[k];
+                while (bits) {
+                    const int y = (w << 5) + (__ffs(bits) - 1);
+                    bits &= bits - 1;
+                    const Id c = st.cls[y];
+                    if (c != kNumbered) st.cls[y] = st.child[c];
+                }
+                if (w == (x >> 5)) st.cls[x] = kNumbered;
+                bits = row_cur[k];
+                uint32_t keep = 0u;
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int y = (w << 5) + b;
+                    const Id c = st.cls[y];
+                    if (c == kNumbered) continue;
+                    keep |= 1u << b;
+                    const Sz old = atomicAdd(&st.sz[c], (Sz)1 << Tr::kShift);
+                    if ((old >> Tr::kShift) == 0) am |= 1u << b;
+                    if (c == f)
+                        atomicMin(&sc->front_min[slot], (unsigned)y);
+                    else if (c == g)
+                        atomicMin(&sc->second_min[slot], (unsigned)y);
+                }
+                row_cur[k] = keep;
+            }
+            amask[k] = am;
+        }
+        __syncthreads();  // A
+
+        // ---- phase D: next pivot (uniform decision)
+        const unsigned fmin = sc->front_min[slot];
+        const unsigned gmin = sc->second_min[slot];
+        const bool fempty = (fsz == 1);
+        int mode;  // 0 pivot known, 1 scan class f, 2 scan class g, 3 finished
+        unsigned xn = 0;
+        Id target = 0;
+        if (fmin != kNoVertex) {
+            mode = 0;
+            xn = fmin;
+        } else if (!fempty) {
+            mode = 1;
+            target = f;
+        } else if (g == kNone) {
+            mode = 3;
+        } else if (gmin != kNoVertex) {
+            mode = 0;
+            xn = gmin;
+        } else {
+            mode = 2;
+            target = g;
+        }
+        if (mode == 0) {
+#pragma unroll
+            for (int k = 0; k < WPT; ++k) {
+                const int w = k * T + t;
+                row_nxt[k] = w < wn ? row_word(rows, stride, (int)xn, w, wn, lastmask) : 0u;
+            }
+        }
+
+        // ---- phase A: allocate / link split classes
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+            const int w = k * T + t;
+            uint32_t am = amask[k];
+            while (am) {
+                const int y = (w << 5) + (__ffs(am) - 1);
+                am &= am - 1;
+                const Id c = st.cls[y];  // class before this step's move (relabel is deferred)
+                const Sz s = st.sz[c];
+                const Sz mv = s >> Tr::kShift;
+                const Sz size = (s & Tr::kMask) - (c == f ? 1 : 0);
+                if (mv == size) {
+                    st.child[c] = c;
+                    st.sz[c] = size;
+                    if (fempty && c == g) {
+                        st.cnext[HEAD] = g;
+                        st.cprev[g] = HEAD;
+                    }
+                } else {
+                    const int idx = atomicSub(&sc->free_top, 1) - 1;
+                    const Id cn = st.freel[idx];
+                    st.child[c] = cn;
+                    st.sz[cn] = mv;
+                    st.sz[c] = size - mv;
+                    Id p = st.cprev[c];
+                    if (fempty && p == f) p = HEAD;
+                    st.cnext[p] = cn;
+                    st.cprev[cn] = p;
+                    st.cnext[cn] = c;
+                    st.cprev[c] = cn;
+                }
+            }
+        }
+        if (t == 0) {
+            if (fmin == kNoVertex) st.sz[f] = fsz - 1;
+            if (fempty) {
+                pending_free = f;
+                if (g == kNone || gmin == kNoVertex) {
+                    st.cnext[HEAD] = g;
+                    if (g != kNone) st.cprev[g] = HEAD;
+                }
+            }
+            sc->front_min[slot ^ 1] = kNoVertex;
+            sc->second_min[slot ^ 1] = kNoVertex;
+        }
+        // class scan for the next pivot, overlapping phase A (cls is not written there)
+        if (mode == 1 || mode == 2) {
+            unsigned best = kNoVertex;
+            for (int v = t; v < n; v += T)
+                if (st.cls[v] == target) {
+                    best = (unsigned)v;
+                    break;
+                }
+            best = __reduce_min_sync(0xFFFFFFFFu, best);
+            if ((t & 31) == 0) sc->red[t >> 5] = best;
+        }
+        __syncthreads();  // B
+        if (mode == 3) break;
+        if (mode != 0) {
+            const unsigned r = (t & 31) < (T / 32) ? sc->red[t & 31] : kNoVertex;
+            xn = __reduce_min_sync(0xFFFFFFFFu, r);
+#pragma unroll
+            for (int k = 0; k < WPT; ++k) {
+                const int w = k * T + t;
+                row_nxt[k] = w < wn ? row_word(rows, stride, (int)xn, w, wn, lastmask) : 0u;
+            }
+        }
+        x = (int)xn;
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+            row_prev[k] = row_cur[k];
+            row_cur[k] = row_nxt[k];
+        }
+    }
+}
+
+}  // namespace cg

@@ -1,0 +1,75 @@
+"""GPU parity of the batched dense path (many graphs per launch)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import graphgen as gg  # noqa: E402
+import oracle  # noqa: E402
+from paper_1508_06329_gb300 import binding as B  # noqa: E402
+
+from gpu_util import DEV, to_dev  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def run_batch(ctx, graphs, offsets=None):
+    tens = [to_dev(g) for g in graphs]
+    res = torch.full((len(graphs), 4), -7, dtype=torch.int32, device=DEV)
+    total = sum(g.n for g in graphs) if offsets is None else int(max(o + g.n for o, g in zip(offsets, graphs)))
+    orders = torch.full((max(total, 1),), -7, dtype=torch.int32, device=DEV)
+    B.chordal_test_batch(ctx, [(t, g.n) for t, g in zip(tens, graphs)], res, orders, offsets)
+    torch.cuda.synchronize()
+    return res.cpu().numpy(), orders.cpu().numpy()
+
+
+def check(graphs, res, orders, offsets=None):
+    off = 0
+    for k, g in enumerate(graphs):
+        want = oracle.chordal_test(g)
+        o = off if offsets is None else offsets[k]
+        assert tuple(res[k].tolist()) == want.witness, k
+        assert np.array_equal(orders[o:o + g.n], want.order), k
+        off += g.n
+
+
+def test_batch_mixed_sizes(ctx):
+    graphs = gg.batch_dense(96, seed=5)
+    res, orders = run_batch(ctx, graphs)
+    check(graphs, res, orders)
+
+
+def test_batch_with_empty_and_tiny(ctx):
+    graphs = [gg.empty_dense(0), gg.empty_dense(1), gg.cycle(4), gg.clique(3), gg.empty_dense(0),
+              gg.subtree_dense(50, 10, 1)]
+    res, orders = run_batch(ctx, graphs)
+    check(graphs, res, orders)
+
+
+def test_batch_order_offsets(ctx):
+    graphs = [gg.subtree_dense(40, 8, 2), gg.cycle(6), gg.subtree_dense(33, 5, 3)]
+    offsets = [100, 3, 50]
+    res, orders = run_batch(ctx, graphs, offsets)
+    check(graphs, res, orders, offsets)
+
+
+def test_batch_large_pair(ctx):
+    g, h, _ = gg.large_dense_pair()
+    res, orders = run_batch(ctx, [g, h])
+    check([g, h], res, orders)
+
+
+def test_batch_workload_full(ctx):
+    """4,096 graphs, N log-uniform in [16, 2048] (the batched workload)."""
+    graphs = gg.batch_dense(4096)
+    res, orders = run_batch(ctx, graphs)
+    check(graphs, res, orders)
