@@ -184,15 +184,16 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
     const DenseDesc d = desc_of(g, 0, 0);
     if (n > 0) {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
-        rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, plan.wide_ids ? at<void>(ctx, o_gstate) : nullptr,
-                                 at<int>(ctx, o_counter), stream);
+        rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, res ? parent : nullptr,
+                                 plan.wide_ids ? at<void>(ctx, o_gstate) : nullptr, at<int>(ctx, o_counter), stream);
         if (rc) return rc;
         ctx->launches += 1;
     }
     if (!res) return CG_OK;
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
     unsigned long long *key = at<unsigned long long>(ctx, o_key);
-    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, key, ctx->num_sms, stream))) return rc;
+    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, true, key, ctx->num_sms, stream)))
+        return rc;
     ctx->launches += n > 0 ? 2 : 1;
     return finalize_launch(nullptr, d, 1, key, order, parent, res, stream);
 }
@@ -307,7 +308,8 @@ int cg_peo_check_dense(cg_context *ctx, const cg_dense *g, const int32_t *order,
     const DenseDesc d = desc_of(g, 0, 0);
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
     if ((rc = invert_order_launch(nullptr, d, 1, nullptr, n, order, pos, ctx->num_sms, stream))) return rc;
-    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, par, key, ctx->num_sms, stream))) return rc;
+    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, par, false, key, ctx->num_sms, stream)))
+        return rc;
     ctx->launches += n > 0 ? 3 : 1;
     return finalize_launch(nullptr, d, 1, key, order, par, res, stream);
 }
@@ -404,14 +406,15 @@ int cg_chordal_test_batch(cg_context *ctx, const cg_dense *graphs, int32_t count
     const DenseDesc none{};
     {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
-        if ((rc = lexbfs_dense_launch(plan, ddesc, none, count, ctas, order, pos,
+        if ((rc = lexbfs_dense_launch(plan, ddesc, none, count, ctas, order, pos, parent,
                                       plan.wide_ids ? at<void>(ctx, o_gstate) : nullptr, at<int>(ctx, o_counter),
                                       stream)))
             return rc;
         ctx->launches += 1;
     }
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
-    if ((rc = peo_dense_launch(ddesc, none, count, dvoff, total, order, pos, parent, keys, ctx->num_sms, stream)))
+    if ((rc = peo_dense_launch(ddesc, none, count, dvoff, total, order, pos, parent, true, keys, ctx->num_sms,
+                               stream)))
         return rc;
     ctx->launches += total > 0 ? 2 : 1;
     return finalize_launch(ddesc, none, count, keys, order, parent, res, stream);

@@ -24,14 +24,18 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan);
 // Runs LexBFS for `count` graphs, one CTA each (grid = min(count, ctas)).
 // descs: device array, or nullptr to use `single` (count must be 1).
 // work_counter: device int, zeroed by the launcher (dynamic graph hand-out).
+// parent (nullable) receives p(v) for every vertex, recorded during the search.
 int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
-                        int32_t *order, int32_t *pos, void *gstate, int *work_counter, cudaStream_t stream);
+                        int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
+                        cudaStream_t stream);
 
 // ---- dense perfect-elimination check (peo_dense.cu)
 // keys: device u64[count], set to ~0 by the launcher.
+// parent_known: parent[] already holds p(v) (from the search); otherwise the
+// kernel computes it from the rows and writes it.
 int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
-                     const int32_t *order, const int32_t *pos, int32_t *parent, unsigned long long *keys,
-                     int num_sms, cudaStream_t stream);
+                     const int32_t *order, const int32_t *pos, int32_t *parent, bool parent_known,
+                     unsigned long long *keys, int num_sms, cudaStream_t stream);
 
 // pos[order[i]] = i for every graph (order values outside 0..n-1 are skipped).
 int invert_order_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,

@@ -12,11 +12,12 @@ constexpr size_t kSmemLimit = 227 * 1024;   // opt-in dynamic shared memory per 
 constexpr int kSmemMaxN = 16384;             // 16-bit ids
 constexpr int kWideMaxN = 131072;            // 32-bit ids: 4 words per thread at 1024 threads
 
-template <typename Id, int T, int WPT, bool ROWS_SMEM>
+template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM>
 __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
                                                          int count, int32_t *__restrict__ order,
-                                                         int32_t *__restrict__ pos, unsigned char *gstate,
-                                                         size_t gstate_stride, int *work_counter) {
+                                                         int32_t *__restrict__ pos, int32_t *__restrict__ parent,
+                                                         unsigned char *gstate, size_t gstate_stride,
+                                                         int *work_counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     LexScalars *sc = reinterpret_cast<LexScalars *>(smem);
     unsigned char *free_smem = smem + kLexScalarBytes;
@@ -38,6 +39,7 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
         }
         const uint32_t *rows = d.rows;
         int stride = d.words;
+        if (!ROWS_SMEM) prefetch_range_l2<T>(d.rows, (size_t)n * d.words * sizeof(uint32_t));
         if (ROWS_SMEM) {
             const int wn = (n + 31) >> 5;
             uint32_t *srows = reinterpret_cast<uint32_t *>(p);
@@ -50,19 +52,21 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
             stride = wn;
             __syncthreads();
         }
-        lexbfs_cta<Id, T, WPT>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr);
+        lexbfs_cta<Id, T, WPT, LPW>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr,
+                               parent ? parent + d.vbase : nullptr);
         __syncthreads();
         if (count == 1) break;
     }
 }
 
-template <typename Id, int T, int WPT, bool ROWS_SMEM>
+template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM>
 int launch_variant(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
-                   int32_t *order, int32_t *pos, void *gstate, int *work_counter, cudaStream_t stream) {
-    auto kern = lexbfs_dense_kernel<Id, T, WPT, ROWS_SMEM>;
+                   int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
+                   cudaStream_t stream) {
+    auto kern = lexbfs_dense_kernel<Id, T, WPT, LPW, ROWS_SMEM>;
     CG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes));
     if (count > 1) CG_CUDA_TRY(cudaMemsetAsync(work_counter, 0, sizeof(int), stream));
-    kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, single, count, order, pos,
+    kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, single, count, order, pos, parent,
                                                static_cast<unsigned char *>(gstate), plan.gstate_bytes,
                                                work_counter);
     CG_LAUNCH_CHECK("lexbfs_dense_kernel");
@@ -83,7 +87,7 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
         const size_t rows = (size_t)n * wn * 4;
         p.wide_ids = false;
         p.rows_smem = kLexScalarBytes + state + rows <= kSmemLimit;
-        int th = n <= 512 ? 128 : (n <= 2048 ? 256 : 512);
+        int th = n <= 512 ? 128 : (n <= 2048 ? 256 : (n <= 8192 ? 512 : 1024));
         if (threads_override) th = threads_override;
         // words per thread must cover the row
         while ((int64_t)th * (th == 128 ? 4 : th == 256 ? 2 : 1) < wn) th *= 2;
@@ -104,34 +108,25 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
 }
 
 int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
-                        int32_t *order, int32_t *pos, void *gstate, int *work_counter, cudaStream_t stream) {
+                        int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
+                        cudaStream_t stream) {
     if (count <= 0) return CG_OK;
     ctas = std::max(1, std::min(ctas, count));
     if (plan.wide_ids)
-        return launch_variant<uint32_t, 1024, 4, false>(plan, descs, single, count, ctas, order, pos, gstate,
+        return launch_variant<uint32_t, 1024, 4, 1, false>(plan, descs, single, count, ctas, order, pos, parent, gstate,
                                                          work_counter, stream);
     switch (plan.threads) {
         case 128:
-            return plan.rows_smem ? launch_variant<uint16_t, 128, 4, true>(plan, descs, single, count, ctas, order,
-                                                                           pos, nullptr, work_counter, stream)
-                                  : launch_variant<uint16_t, 128, 4, false>(plan, descs, single, count, ctas,
-                                                                            order, pos, nullptr, work_counter,
-                                                                            stream);
+            return plan.rows_smem ? launch_variant<uint16_t, 128, 4, 1, true>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream)
+                                  : launch_variant<uint16_t, 128, 4, 1, false>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream);
         case 256:
-            return plan.rows_smem ? launch_variant<uint16_t, 256, 2, true>(plan, descs, single, count, ctas, order,
-                                                                           pos, nullptr, work_counter, stream)
-                                  : launch_variant<uint16_t, 256, 2, false>(plan, descs, single, count, ctas,
-                                                                            order, pos, nullptr, work_counter,
-                                                                            stream);
+            return plan.rows_smem ? launch_variant<uint16_t, 256, 2, 1, true>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream)
+                                  : launch_variant<uint16_t, 256, 2, 1, false>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream);
         case 512:
-            return plan.rows_smem ? launch_variant<uint16_t, 512, 1, true>(plan, descs, single, count, ctas, order,
-                                                                           pos, nullptr, work_counter, stream)
-                                  : launch_variant<uint16_t, 512, 1, false>(plan, descs, single, count, ctas,
-                                                                            order, pos, nullptr, work_counter,
-                                                                            stream);
+            return plan.rows_smem ? launch_variant<uint16_t, 512, 1, 1, true>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream)
+                                  : launch_variant<uint16_t, 512, 1, 1, false>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream);
         default:
-            return launch_variant<uint16_t, 1024, 1, false>(plan, descs, single, count, ctas, order, pos, nullptr,
-                                                            work_counter, stream);
+            return launch_variant<uint16_t, 1024, 1, 2, false>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream);
     }
 }
 

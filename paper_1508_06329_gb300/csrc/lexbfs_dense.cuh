@@ -26,7 +26,15 @@
 //     collected while splitting), or of the class after it when the top class
 //     empties; only when neither class lost members is a class scan needed.
 //     A known pivot's row is requested right after the first barrier, so its
-//     load overlaps the list update.  Two __syncthreads per step.
+//     load overlaps the list update.  Two __syncthreads per step;
+//   * a shared bitmask of numbered vertices filters each pivot row, so only
+//     unnumbered neighbours are visited, and the deferred relabel and the
+//     split share one loop over a word's bits;
+//   * every moved vertex y records parent[y] = x; the last pivot that moves y
+//     is its neighbour with the largest order index below its own, i.e.
+//     p(y) of the perfect-elimination check (Section 5.3), so the check does
+//     not rescan rows to find parents;
+//   * the graph's rows are bulk-prefetched into L2 when the CTA starts.
 #pragma once
 #include "common.cuh"
 
@@ -55,6 +63,7 @@ struct LexState {
     Id *freel;                      // [n]     stack of unused class ids
     Id *cnext;                      // [n + 1] class list; index n is the head sentinel
     Id *cprev;                      // [n + 1]
+    uint32_t *numbered;             // [ceil(n/32)] bit v set once v is visited
 };
 
 struct LexScalars {
@@ -71,6 +80,8 @@ template <typename Id>
 __host__ __device__ inline size_t lex_state_bytes(int n) {
     using Sz = typename IdTraits<Id>::Sz;
     size_t b = (size_t)n * sizeof(Sz) + (size_t)n * sizeof(Id) * 3 + (size_t)(n + 1) * sizeof(Id) * 2;
+    b = (b + 15) & ~size_t(15);
+    b += (size_t)((n + 31) / 32) * sizeof(uint32_t);   // numbered bitmask
     return (b + 15) & ~size_t(15);
 }
 
@@ -85,6 +96,8 @@ __device__ inline LexState<Id> lex_state_carve(unsigned char *base, int n) {
     s.freel = p + 2 * (size_t)n;
     s.cnext = p + 3 * (size_t)n;
     s.cprev = p + 4 * (size_t)n + 1;
+    size_t b = (size_t)n * sizeof(Sz) + (size_t)n * sizeof(Id) * 3 + (size_t)(n + 1) * sizeof(Id) * 2;
+    s.numbered = reinterpret_cast<uint32_t *>(base + ((b + 15) & ~size_t(15)));
     return s;
 }
 
@@ -97,23 +110,57 @@ __device__ __forceinline__ uint32_t row_word(const uint32_t *__restrict__ rows, 
     return w == wn - 1 ? (v & lastmask) : v;
 }
 
+// Asks L2 to fetch [p, p + bytes) (bulk prefetch, no completion tracking).
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Spreads bulk L2 prefetches of a contiguous range over the CTA's threads.
+template <int T>
+__device__ __forceinline__ void prefetch_range_l2(const void *base, size_t bytes) {
+    constexpr uint32_t kChunk = 32768;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(base);
+    const uintptr_t a16 = (a + 15) & ~uintptr_t(15);
+    if (bytes <= (size_t)(a16 - a)) return;
+    size_t left = (bytes - (a16 - a)) & ~size_t(15);
+    const size_t chunks = (left + kChunk - 1) / kChunk;
+    for (size_t c = threadIdx.x; c < chunks; c += T) {
+        const size_t off = c * kChunk;
+        const uint32_t len = (uint32_t)((left - off) < kChunk ? (left - off) : kChunk);
+        prefetch_l2_bulk(reinterpret_cast<const void *>(a16 + off), len);
+    }
+}
+
 // One CTA computes the LexBFS order of one graph.  rows/stride address the
-// adjacency (global memory, or a compact shared-memory copy).
-template <typename Id, int T, int WPT>
+// adjacency (global memory, or a compact shared-memory copy).  parent may be
+// null; otherwise parent[v] receives p(v) (or -1 when v has no earlier
+// neighbour).  LPW threads share each row word (thread t takes bit slice
+// t % LPW of word t / LPW + k * T / LPW), which shortens the serial bit loop.
+template <typename Id, int T, int WPT, int LPW>
 __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n, LexState<Id> st,
-                           LexScalars *sc, int32_t *__restrict__ order, int32_t *__restrict__ pos) {
+                           LexScalars *sc, int32_t *__restrict__ order, int32_t *__restrict__ pos,
+                           int32_t *__restrict__ parent) {
     using Tr = IdTraits<Id>;
     using Sz = typename Tr::Sz;
     const Id kNumbered = (Id)~(Id)0;
     const Id kNone = (Id)(kNumbered - 1);
     const int t = threadIdx.x;
     if (n <= 0) return;
+    constexpr int kGroups = T / LPW;            // word slots per k
+    constexpr int kSlice = 32 / LPW;            // bits per thread
+    const int wt = t / LPW;
+    const uint32_t part = LPW == 1 ? 0xFFFFFFFFu
+                                   : (((1u << kSlice) - 1u) << ((t % LPW) * kSlice));
     const Id HEAD = (Id)n;
     const int wn = (n + 31) >> 5;
     const uint32_t lastmask = (n & 31) ? ((1u << (n & 31)) - 1u) : 0xFFFFFFFFu;
 
-    for (int v = t; v < n; v += T) st.cls[v] = 0;
+    for (int v = t; v < n; v += T) {
+        st.cls[v] = 0;
+        if (parent) parent[v] = -1;
+    }
     for (int k = t; k < n - 1; k += T) st.freel[k] = (Id)(k + 1);
+    for (int w = t; w < wn; w += T) st.numbered[w] = 0u;
     if (t == 0) {
         st.sz[0] = (Sz)n;
         st.cnext[HEAD] = 0;
@@ -127,8 +174,8 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
     int x = 0;
 #pragma unroll
     for (int k = 0; k < WPT; ++k) {
-        const int w = k * T + t;
-        row_cur[k] = w < wn ? row_word(rows, stride, x, w, wn, lastmask) : 0u;
+        const int w = k * kGroups + wt;
+        row_cur[k] = w < wn ? row_word(rows, stride, x, w, wn, lastmask) & part : 0u;
         row_prev[k] = 0u;
         row_nxt[k] = 0u;
         amask[k] = 0u;
@@ -154,34 +201,38 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
         }
 #pragma unroll
         for (int k = 0; k < WPT; ++k) {
-            const int w = k * T + t;
+            const int w = k * kGroups + wt;
             uint32_t am = 0u;
             if (w < wn) {
-                uint32_t bits = row_prev[k];
-                while (bits) {
-                    const int y = (w << 5) + (__ffs(bits) - 1);
-                    bits &= bits - 1;
-                    const Id c = st.cls[y];
-                    if (c != kNumbered) st.cls[y] = st.child[c];
-                }
-                if (w == (x >> 5)) st.cls[x] = kNumbered;
-                bits = row_cur[k];
-                uint32_t keep = 0u;
+                const uint32_t prev = row_prev[k];
+                uint32_t nb = st.numbered[w];
+                const uint32_t cur = row_cur[k] & ~nb;  // unnumbered neighbours of x
+                uint32_t bits = prev | cur;
                 while (bits) {
                     const int b = __ffs(bits) - 1;
+                    const uint32_t bit = 1u << b;
                     bits &= bits - 1;
                     const int y = (w << 5) + b;
-                    const Id c = st.cls[y];
-                    if (c == kNumbered) continue;
-                    keep |= 1u << b;
-                    const Sz old = atomicAdd(&st.sz[c], (Sz)1 << Tr::kShift);
-                    if ((old >> Tr::kShift) == 0) am |= 1u << b;
-                    if (c == f)
-                        atomicMin(&sc->front_min[slot], (unsigned)y);
-                    else if (c == g)
-                        atomicMin(&sc->second_min[slot], (unsigned)y);
+                    Id c = st.cls[y];
+                    if (prev & bit) {  // moved by the previous pivot: finish its relabel
+                        c = st.child[c];
+                        st.cls[y] = c;
+                    }
+                    if (cur & bit) {
+                        const Sz old = atomicAdd(&st.sz[c], (Sz)1 << Tr::kShift);
+                        if ((old >> Tr::kShift) == 0) am |= bit;
+                        if (c == f)
+                            atomicMin(&sc->front_min[slot], (unsigned)y);
+                        else if (c == g)
+                            atomicMin(&sc->second_min[slot], (unsigned)y);
+                        if (parent) parent[y] = x;
+                    }
                 }
-                row_cur[k] = keep;
+                if (w == (x >> 5) && ((part >> (x & 31)) & 1u)) {
+                    st.cls[x] = kNumbered;
+                    st.numbered[w] = nb | (1u << (x & 31));
+                }
+                row_cur[k] = cur;
             }
             amask[k] = am;
         }
@@ -212,15 +263,15 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
         if (mode == 0) {
 #pragma unroll
             for (int k = 0; k < WPT; ++k) {
-                const int w = k * T + t;
-                row_nxt[k] = w < wn ? row_word(rows, stride, (int)xn, w, wn, lastmask) : 0u;
+                const int w = k * kGroups + wt;
+                row_nxt[k] = w < wn ? row_word(rows, stride, (int)xn, w, wn, lastmask) & part : 0u;
             }
         }
 
         // ---- phase A: allocate / link split classes
 #pragma unroll
         for (int k = 0; k < WPT; ++k) {
-            const int w = k * T + t;
+            const int w = k * kGroups + wt;
             uint32_t am = amask[k];
             while (am) {
                 const int y = (w << 5) + (__ffs(am) - 1);
@@ -281,8 +332,8 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             xn = __reduce_min_sync(0xFFFFFFFFu, r);
 #pragma unroll
             for (int k = 0; k < WPT; ++k) {
-                const int w = k * T + t;
-                row_nxt[k] = w < wn ? row_word(rows, stride, (int)xn, w, wn, lastmask) : 0u;
+                const int w = k * kGroups + wt;
+                row_nxt[k] = w < wn ? row_word(rows, stride, (int)xn, w, wn, lastmask) & part : 0u;
             }
         }
         x = (int)xn;

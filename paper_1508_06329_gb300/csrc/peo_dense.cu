@@ -2,7 +2,8 @@
 //
 // For every vertex v (one warp per vertex, all graphs of a batch in one grid):
 //   p(v)  = the neighbour of v with the largest order index below pos(v)
-//           (the paper's preparationLNandP kernel);
+//           (the paper's preparationLNandP kernel) — taken from the LexBFS
+//           kernel, which records it, or computed here for a given order;
 //   bad   = (LN_v - {p}) \ N(p), evaluated word by word as row_v & ~row_p and
 //           kept only for bits u != p with pos(u) < pos(v) (the paper's
 //           testing kernel, with p itself excluded);
@@ -20,6 +21,9 @@ namespace {
 
 constexpr int kPeoThreads = 256;
 
+constexpr int kRC = 16;   // row words per lane held in registers (512 words = 16,384 vertices per chunk)
+
+template <bool PARENT_KNOWN>
 __global__ void __launch_bounds__(kPeoThreads) peo_dense_kernel(const DenseDesc *__restrict__ descs,
                                                                 DenseDesc single, int count,
                                                                 const int64_t *__restrict__ voff, int64_t total,
@@ -48,38 +52,62 @@ __global__ void __launch_bounds__(kPeoThreads) peo_dense_kernel(const DenseDesc 
         const int pv = __ldg(pos_g + v);
         const uint32_t *rv = d.rows + (size_t)v * d.words;
 
-        int best = -1;
-        for (int w = lane; w < wn; w += 32) {
-            uint32_t bits = __ldg(rv + w);
-            if (w == wn - 1) bits &= lastmask;
-            while (bits) {
-                const int u = (w << 5) + (__ffs(bits) - 1);
-                bits &= bits - 1;
-                const int pu = __ldg(pos_g + u);
-                if (pu < pv && pu > best) best = pu;
-            }
-        }
-        best = __reduce_max_sync(0xFFFFFFFFu, best);
-        const int p = best >= 0 ? __ldg(order + d.obase + best) : -1;
-        if (lane == 0) parent[d.vbase + v] = p;
-        if (p < 0) continue;
-
-        const uint32_t *rp = d.rows + (size_t)p * d.words;
-        unsigned umin = 0xFFFFFFFFu;
-        for (int w = lane; w < wn; w += 32) {
-            uint32_t bits = __ldg(rv + w) & ~__ldg(rp + w);
-            if (w == wn - 1) bits &= lastmask;
-            while (bits) {
-                const int u = (w << 5) + (__ffs(bits) - 1);
-                bits &= bits - 1;
-                if (u != p && __ldg(pos_g + u) < pv) {
-                    umin = (unsigned)u;
-                    break;
+        int p;
+        if (PARENT_KNOWN) {
+            p = __ldg(parent + d.vbase + v);
+        } else {
+            int best = -1;
+            for (int w0 = 0; w0 < wn; w0 += 32 * kRC) {
+                uint32_t a[kRC];
+#pragma unroll
+                for (int k = 0; k < kRC; ++k) {
+                    const int w = w0 + k * 32 + lane;
+                    a[k] = w < wn ? __ldg(rv + w) : 0u;
+                    if (w == wn - 1) a[k] &= lastmask;
+                }
+#pragma unroll
+                for (int k = 0; k < kRC; ++k) {
+                    uint32_t bits = a[k];
+                    const int w = w0 + k * 32 + lane;
+                    while (bits) {
+                        const int u = (w << 5) + (__ffs(bits) - 1);
+                        bits &= bits - 1;
+                        const int pu = __ldg(pos_g + u);
+                        if (pu < pv && pu > best) best = pu;
+                    }
                 }
             }
-            if (umin != 0xFFFFFFFFu) break;
+            best = __reduce_max_sync(0xFFFFFFFFu, best);
+            p = best >= 0 ? __ldg(order + d.obase + best) : -1;
+            if (lane == 0) parent[d.vbase + v] = p;
         }
-        umin = __reduce_min_sync(0xFFFFFFFFu, umin);
+        if (p < 0) continue;
+
+        // LN_v - {p} ⊆ N(p): scan row_v & ~row_p for an earlier vertex other than p
+        const uint32_t *rp = d.rows + (size_t)p * d.words;
+        unsigned umin = 0xFFFFFFFFu;
+        for (int w0 = 0; w0 < wn && umin == 0xFFFFFFFFu; w0 += 32 * kRC) {
+            uint32_t a[kRC], b[kRC];
+#pragma unroll
+            for (int k = 0; k < kRC; ++k) {
+                const int w = w0 + k * 32 + lane;
+                a[k] = w < wn ? __ldg(rv + w) : 0u;
+                b[k] = w < wn ? __ldg(rp + w) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < kRC; ++k) {
+                const int w = w0 + k * 32 + lane;
+                uint32_t bits = a[k] & ~b[k];
+                if (w == wn - 1) bits &= lastmask;
+                if (w == (p >> 5)) bits &= ~(1u << (p & 31));
+                while (bits && umin == 0xFFFFFFFFu) {
+                    const int u = (w << 5) + (__ffs(bits) - 1);
+                    bits &= bits - 1;
+                    if (__ldg(pos_g + u) < pv) umin = (unsigned)u;
+                }
+            }
+            umin = __reduce_min_sync(0xFFFFFFFFu, umin);
+        }
         if (lane == 0 && umin != 0xFFFFFFFFu)
             atomicMin(keys + gi, ((unsigned long long)(unsigned)pv << 32) | umin);
     }
@@ -139,16 +167,20 @@ int invert_order_launch(const DenseDesc *descs, DenseDesc single, int count, con
 }
 
 int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
-                     const int32_t *order, const int32_t *pos, int32_t *parent, unsigned long long *keys,
-                     int num_sms, cudaStream_t stream) {
+                     const int32_t *order, const int32_t *pos, int32_t *parent, bool parent_known,
+                     unsigned long long *keys, int num_sms, cudaStream_t stream) {
     if (count <= 0) return CG_OK;
     CG_CUDA_TRY(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * count, stream));
     if (total <= 0) return CG_OK;
     const int64_t warps_needed = total;
     const int64_t blocks_needed = ceil_div(warps_needed, kPeoThreads / 32);
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, (int64_t)num_sms * 8));
-    peo_dense_kernel<<<blocks, kPeoThreads, 0, stream>>>(descs, single, count, voff, total, order, pos, parent,
-                                                         keys);
+    if (parent_known)
+        peo_dense_kernel<true><<<blocks, kPeoThreads, 0, stream>>>(descs, single, count, voff, total, order, pos,
+                                                                   parent, keys);
+    else
+        peo_dense_kernel<false><<<blocks, kPeoThreads, 0, stream>>>(descs, single, count, voff, total, order, pos,
+                                                                    parent, keys);
     CG_LAUNCH_CHECK("peo_dense_kernel");
     return CG_OK;
 }
