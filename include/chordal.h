@@ -148,6 +148,28 @@ int cg_chordal_test_batch(cg_context *ctx, const cg_dense *graphs, int32_t count
                           int32_t *orders, const int64_t *order_offsets, cudaStream_t stream);
 
 /*
+ * The dense test without any memory allocation (the paper has no counterpart;
+ * this is a deployment aid).  For callers that cannot allocate device memory
+ * when they call in — a plugin whose host application owns the device memory
+ * and forbids allocations after start-up, a latency-critical loop that must
+ * never wait in an allocator, or a caller that keeps no cg_context.  Same
+ * kernels and results as cg_chordal_test_dense, but the scratch (positions,
+ * parents, an order buffer when `order` is NULL, the witness key) comes from
+ * one fixed array in the library's device image, about 193 KiB, held on every
+ * GPU that loads the library until the process exits.
+ *   g      device graph with n <= 16384 (larger n: CG_EINVAL, use
+ *          cg_chordal_test_dense)
+ *   res    device cg_result (written)
+ *   order  device int32[n] (written) or NULL
+ * Works on the current CUDA device.  All calls share the array and it keeps
+ * the last call's contents (the witness key is reset by every call); calls
+ * that overlap on the GPU race on it, so issue them on one stream.  The first
+ * call on each device resolves the array's address (cudaGetSymbolAddress);
+ * make that first call before any stream capture begins.
+ */
+int cg_chordal_test_dense_noalloc(const cg_dense *g, cg_result *res, int32_t *order, cudaStream_t stream);
+
+/*
  * Per-phase timing (tracing aid; not part of the paper).  When enabled, each
  * call records CUDA events on its stream around the LexBFS launch and around
  * the check (check + finalize launches).  cg_profile_read waits for the

@@ -66,6 +66,7 @@ SIGNATURES = {
     "cg_chordal_test_dense": ([P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_dense_host": ([P, I32, I32, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_batch": ([P, P, I32, P, P, P, P], ctypes.c_int),
+    "cg_chordal_test_dense_noalloc": ([P, P, P, P], ctypes.c_int),
     "cg_profile_enable": ([P, I32], ctypes.c_int),
     "cg_profile_read": ([P, P], ctypes.c_int),
 }
@@ -114,6 +115,7 @@ cg_peo_check_dense = _fn("cg_peo_check_dense")
 cg_chordal_test_dense = _fn("cg_chordal_test_dense")
 cg_chordal_test_dense_host = _fn("cg_chordal_test_dense_host")
 cg_chordal_test_batch = _fn("cg_chordal_test_batch")
+cg_chordal_test_dense_noalloc = _fn("cg_chordal_test_dense_noalloc")
 cg_profile_enable = _fn("cg_profile_enable")
 cg_profile_read = _fn("cg_profile_read")
 
