@@ -133,6 +133,33 @@ int cg_chordal_test_dense_host(cg_context *ctx, int32_t n, int32_t words_per_row
                                cudaStream_t stream);
 
 /*
+ * LexBFS order of a CSR graph (Section 4.2 in its O(N + M) form: each class a
+ * list sorted by id, only the pivot's neighbours move).  One warp walks the n
+ * steps with the partition state in the context workspace (about 84 B per
+ * vertex, L2-resident for n ~ 1M).
+ *   g      device CSR graph (sorted, symmetric, no loops; checked only when
+ *          cfg.validate, which then synchronises the stream)
+ *   order  device int32[n] (written);  pos  device int32[n] (written) or NULL
+ */
+int cg_lexbfs_order_csr(cg_context *ctx, const cg_csr *g, int32_t *order, int32_t *pos, cudaStream_t stream);
+
+/* Perfect-elimination check of a caller-given order on a CSR graph (Sections
+ * 5.3, 6.2): LN_v - {p(v)} ⊆ N(p(v)) by binary search in p's sorted row.
+ *   order device int32[n] permutation; parent device int32[n] or NULL;
+ *   res device cg_result */
+int cg_peo_check_csr(cg_context *ctx, const cg_csr *g, const int32_t *order, int32_t *parent, cg_result *res,
+                     cudaStream_t stream);
+
+/* The whole test on one CSR graph.  res device cg_result; order device
+ * int32[n] or NULL. */
+int cg_chordal_test_csr(cg_context *ctx, const cg_csr *g, cg_result *res, int32_t *order, cudaStream_t stream);
+
+/* The CSR test with HOST buffers (row_ptr int64[n+1], col int32[nnz]); copies
+ * in, runs, copies the result (and order when non-NULL) out, synchronises. */
+int cg_chordal_test_csr_host(cg_context *ctx, int32_t n, int64_t nnz, const int64_t *host_row_ptr,
+                             const int32_t *host_col, cg_result *host_res, int32_t *host_order, cudaStream_t stream);
+
+/*
  * Many dense graphs in one pass (the batching of independent tests): each
  * graph's LexBFS runs in its own CTA of one persistent launch, graphs handed
  * out largest first; the checks of all graphs share one grid.

@@ -66,6 +66,10 @@ SIGNATURES = {
     "cg_chordal_test_dense": ([P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_dense_host": ([P, I32, I32, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_batch": ([P, P, I32, P, P, P, P], ctypes.c_int),
+    "cg_lexbfs_order_csr": ([P, P, P, P, P], ctypes.c_int),
+    "cg_peo_check_csr": ([P, P, P, P, P, P], ctypes.c_int),
+    "cg_chordal_test_csr": ([P, P, P, P, P], ctypes.c_int),
+    "cg_chordal_test_csr_host": ([P, I32, I64, P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_dense_noalloc": ([P, P, P, P], ctypes.c_int),
     "cg_profile_enable": ([P, I32], ctypes.c_int),
     "cg_profile_read": ([P, P], ctypes.c_int),
@@ -115,6 +119,10 @@ cg_peo_check_dense = _fn("cg_peo_check_dense")
 cg_chordal_test_dense = _fn("cg_chordal_test_dense")
 cg_chordal_test_dense_host = _fn("cg_chordal_test_dense_host")
 cg_chordal_test_batch = _fn("cg_chordal_test_batch")
+cg_lexbfs_order_csr = _fn("cg_lexbfs_order_csr")
+cg_peo_check_csr = _fn("cg_peo_check_csr")
+cg_chordal_test_csr = _fn("cg_chordal_test_csr")
+cg_chordal_test_csr_host = _fn("cg_chordal_test_csr_host")
 cg_chordal_test_dense_noalloc = _fn("cg_chordal_test_dense_noalloc")
 cg_profile_enable = _fn("cg_profile_enable")
 cg_profile_read = _fn("cg_profile_read")
@@ -218,3 +226,40 @@ def chordal_test_batch(ctx: Context, graphs, res, orders=None, order_offsets=Non
         offs = (ctypes.c_int64 * max(count, 1))(*[int(x) for x in order_offsets])
     _check(cg_chordal_test_batch(ctx.handle, arr, count, _ptr(res), _ptr(orders),
                                  offs if offs is not None else None, _stream(stream)))
+
+
+def csr_desc(row_ptr, col, n: int) -> cg_csr:
+    """row_ptr: CUDA int64 tensor [n+1]; col: CUDA int32 tensor [nnz]."""
+    if row_ptr.element_size() != 8 or col.element_size() != 4:
+        raise ValueError("row_ptr must hold int64 and col int32")
+    return cg_csr(n, int(col.numel()), _ptr(row_ptr), _ptr(col) if col.numel() else 0)
+
+
+def lexbfs_order_csr(ctx: Context, row_ptr, col, n: int, order, pos=None, stream=None):
+    d = csr_desc(row_ptr, col, n)
+    _check(cg_lexbfs_order_csr(ctx.handle, ctypes.byref(d), _ptr(order), _ptr(pos), _stream(stream)))
+
+
+def chordal_test_csr(ctx: Context, row_ptr, col, n: int, res, order=None, stream=None):
+    d = csr_desc(row_ptr, col, n)
+    _check(cg_chordal_test_csr(ctx.handle, ctypes.byref(d), _ptr(res), _ptr(order), _stream(stream)))
+
+
+def peo_check_csr(ctx: Context, row_ptr, col, n: int, order, res, parent=None, stream=None):
+    d = csr_desc(row_ptr, col, n)
+    _check(cg_peo_check_csr(ctx.handle, ctypes.byref(d), _ptr(order), _ptr(parent), _ptr(res), _stream(stream)))
+
+
+def chordal_test_csr_host(ctx: Context, row_ptr, col, n: int, order_host=None, stream=None) -> tuple:
+    """row_ptr / col: host numpy arrays (int64 / int32) or CPU tensors."""
+    import numpy as np
+
+    def hp(a):
+        if a is None:
+            return 0
+        return int(a.data_ptr()) if hasattr(a, "data_ptr") else np.ascontiguousarray(a).ctypes.data
+    nnz = int(col.numel() if hasattr(col, "numel") else col.shape[0])
+    out = cg_result()
+    _check(cg_chordal_test_csr_host(ctx.handle, n, nnz, hp(row_ptr), hp(col) if nnz else 0, ctypes.byref(out),
+                                    hp(order_host), _stream(stream)))
+    return out.astuple()

@@ -153,6 +153,15 @@ int check_dense(const cg_dense *g) {
     return CG_OK;
 }
 
+int check_csr(const cg_csr *g) {
+    if (!g) return set_error(CG_EINVAL, "null graph descriptor");
+    if (g->n < 0) return set_error(CG_EINVAL, "n must be >= 0 (got %d)", g->n);
+    if (g->nnz < 0) return set_error(CG_EINVAL, "nnz must be >= 0");
+    if (g->n > 0 && !g->row_ptr) return set_error(CG_EINVAL, "null row_ptr");
+    if (g->nnz > 0 && !g->col) return set_error(CG_EINVAL, "null col");
+    return CG_OK;
+}
+
 DenseDesc desc_of(const cg_dense *g, int64_t vbase, int64_t obase) {
     DenseDesc d;
     d.rows = g->rows;
@@ -194,6 +203,53 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
     unsigned long long *key = at<unsigned long long>(ctx, o_key);
     if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, true, key, ctx->num_sms, stream)))
         return rc;
+    ctx->launches += n > 0 ? 2 : 1;
+    return finalize_launch(nullptr, d, 1, key, order, parent, res, stream);
+}
+
+// Optional layout check of a CSR graph (synchronises the stream).
+int validate_csr(cg_context *ctx, const cg_csr *g, int *flag_dev, cudaStream_t stream) {
+    int rc;
+    if ((rc = validate_csr_launch(g->n, g->nnz, g->row_ptr, g->col, flag_dev, ctx->num_sms, stream))) return rc;
+    int flag = 0;
+    CG_CUDA_TRY(cudaMemcpyAsync(&flag, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    CG_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (flag)
+        return set_error(CG_EINVAL, "CSR layout check failed (flags 0x%x: 1 row_ptr, 2 range, 4 unsorted/duplicate, "
+                                    "8 self-loop, 16 not symmetric)", flag);
+    return CG_OK;
+}
+
+// LexBFS and (optionally) the check for one CSR graph.
+int run_single_csr(cg_context *ctx, const cg_csr *g, int32_t *order_out, int32_t *pos_out, cg_result *res,
+                   cudaStream_t stream) {
+    const int n = g->n;
+    Carve cv;
+    const size_t o_order = cv.take<int32_t>(n);
+    const size_t o_pos = cv.take<int32_t>(n);
+    const size_t o_parent = cv.take<int32_t>(n);
+    const size_t o_key = cv.take<unsigned long long>(1);
+    const size_t o_flag = cv.take<int>(1);
+    const size_t o_state = cv.take<unsigned char>(lexbfs_csr_workspace_bytes(n, n));
+    int rc;
+    if ((rc = ensure_ws(ctx, cv.off))) return rc;
+    if (ctx->cfg.validate && (rc = validate_csr(ctx, g, at<int>(ctx, o_flag), stream))) return rc;
+    int32_t *order = order_out ? order_out : at<int32_t>(ctx, o_order);
+    int32_t *pos = pos_out ? pos_out : at<int32_t>(ctx, o_pos);
+    int32_t *parent = at<int32_t>(ctx, o_parent);
+    if (n > 0) {
+        PhaseTimer pt(ctx, &ctx->ev_lex, stream);
+        if ((rc = lexbfs_csr_launch(n, n, g->row_ptr, g->col, order, pos, parent, at<void>(ctx, o_state),
+                                    ctx->num_sms, stream)))
+            return rc;
+        ctx->launches += 2;
+    }
+    if (!res) return CG_OK;
+    PhaseTimer pt(ctx, &ctx->ev_check, stream);
+    unsigned long long *key = at<unsigned long long>(ctx, o_key);
+    if ((rc = peo_csr_launch(n, g->row_ptr, g->col, order, pos, parent, true, key, ctx->num_sms, stream))) return rc;
+    DenseDesc d{};
+    d.n = n;
     ctx->launches += n > 0 ? 2 : 1;
     return finalize_launch(nullptr, d, 1, key, order, parent, res, stream);
 }
@@ -342,6 +398,82 @@ int cg_chordal_test_dense_host(cg_context *ctx, int32_t n, int32_t words_per_row
     if (bytes_rows) CG_CUDA_TRY(cudaMemcpyAsync(rows, host_rows, bytes_rows, cudaMemcpyHostToDevice, stream));
     cg_dense g{n, words_per_row, rows};
     if ((rc = run_single_dense(ctx, &g, order, nullptr, res, nullptr, stream))) return rc;
+    CG_CUDA_TRY(cudaMemcpyAsync(host_res, res, sizeof(cg_result), cudaMemcpyDeviceToHost, stream));
+    if (host_order && n > 0)
+        CG_CUDA_TRY(cudaMemcpyAsync(host_order, order, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, stream));
+    CG_CUDA_TRY(cudaStreamSynchronize(stream));
+    return CG_OK;
+}
+
+int cg_lexbfs_order_csr(cg_context *ctx, const cg_csr *g, int32_t *order, int32_t *pos, cudaStream_t stream) {
+    int rc;
+    if ((rc = check_ctx(ctx)) || (rc = check_csr(g))) return rc;
+    if (g->n > 0 && !order) return set_error(CG_EINVAL, "null order pointer");
+    return run_single_csr(ctx, g, order, pos, nullptr, stream);
+}
+
+int cg_chordal_test_csr(cg_context *ctx, const cg_csr *g, cg_result *res, int32_t *order, cudaStream_t stream) {
+    int rc;
+    if ((rc = check_ctx(ctx)) || (rc = check_csr(g))) return rc;
+    if (!res) return set_error(CG_EINVAL, "null result pointer");
+    return run_single_csr(ctx, g, order, nullptr, res, stream);
+}
+
+int cg_peo_check_csr(cg_context *ctx, const cg_csr *g, const int32_t *order, int32_t *parent, cg_result *res,
+                     cudaStream_t stream) {
+    int rc;
+    if ((rc = check_ctx(ctx)) || (rc = check_csr(g))) return rc;
+    if (!res) return set_error(CG_EINVAL, "null result pointer");
+    if (g->n > 0 && !order) return set_error(CG_EINVAL, "null order pointer");
+    const int n = g->n;
+    Carve cv;
+    const size_t o_pos = cv.take<int32_t>(n);
+    const size_t o_parent = cv.take<int32_t>(n);
+    const size_t o_key = cv.take<unsigned long long>(1);
+    const size_t o_flag = cv.take<int>(1);
+    if ((rc = ensure_ws(ctx, cv.off))) return rc;
+    if (ctx->cfg.validate && (rc = validate_csr(ctx, g, at<int>(ctx, o_flag), stream))) return rc;
+    int32_t *pos = at<int32_t>(ctx, o_pos);
+    int32_t *par = parent ? parent : at<int32_t>(ctx, o_parent);
+    unsigned long long *key = at<unsigned long long>(ctx, o_key);
+    DenseDesc d{};
+    d.n = n;
+    PhaseTimer pt(ctx, &ctx->ev_check, stream);
+    if ((rc = invert_order_launch(nullptr, d, 1, nullptr, n, order, pos, ctx->num_sms, stream))) return rc;
+    if ((rc = peo_csr_launch(n, g->row_ptr, g->col, order, pos, par, false, key, ctx->num_sms, stream))) return rc;
+    ctx->launches += n > 0 ? 3 : 1;
+    return finalize_launch(nullptr, d, 1, key, order, par, res, stream);
+}
+
+int cg_chordal_test_csr_host(cg_context *ctx, int32_t n, int64_t nnz, const int64_t *host_row_ptr,
+                             const int32_t *host_col, cg_result *host_res, int32_t *host_order, cudaStream_t stream) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!host_res) return set_error(CG_EINVAL, "null host result pointer");
+    cg_csr probe{n, nnz, host_row_ptr, host_col};
+    if ((rc = check_csr(&probe))) return rc;
+    // inputs and outputs sit after the scratch that run_single_csr carves
+    Carve cv;
+    cv.take<int32_t>(n);
+    cv.take<int32_t>(n);
+    cv.take<int32_t>(n);
+    cv.take<unsigned long long>(1);
+    cv.take<int>(1);
+    cv.take<unsigned char>(lexbfs_csr_workspace_bytes(n, n));
+    const size_t o_rp = cv.take<int64_t>((size_t)n + 1);
+    const size_t o_col = cv.take<int32_t>((size_t)nnz);
+    const size_t o_res = cv.take<cg_result>(1);
+    const size_t o_order = cv.take<int32_t>(n);
+    if ((rc = ensure_ws(ctx, cv.off))) return rc;
+    int64_t *rp = at<int64_t>(ctx, o_rp);
+    int32_t *col = at<int32_t>(ctx, o_col);
+    if (n >= 0)
+        CG_CUDA_TRY(cudaMemcpyAsync(rp, host_row_ptr, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, stream));
+    if (nnz > 0) CG_CUDA_TRY(cudaMemcpyAsync(col, host_col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, stream));
+    cg_csr g{n, nnz, rp, col};
+    cg_result *res = at<cg_result>(ctx, o_res);
+    int32_t *order = at<int32_t>(ctx, o_order);
+    if ((rc = run_single_csr(ctx, &g, order, nullptr, res, stream))) return rc;
     CG_CUDA_TRY(cudaMemcpyAsync(host_res, res, sizeof(cg_result), cudaMemcpyDeviceToHost, stream));
     if (host_order && n > 0)
         CG_CUDA_TRY(cudaMemcpyAsync(host_order, order, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, stream));

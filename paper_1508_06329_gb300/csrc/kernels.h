@@ -44,4 +44,16 @@ int invert_order_launch(const DenseDesc *descs, DenseDesc single, int count, con
 int finalize_launch(const DenseDesc *descs, DenseDesc single, int count, const unsigned long long *keys,
                     const int32_t *order, const int32_t *parent, cg_result *res, cudaStream_t stream);
 
+// ---- CSR LexBFS (lexbfs_csr.cu): one warp per graph, state in `ws`
+size_t lexbfs_csr_workspace_bytes(int64_t n, int64_t max_deg);
+int lexbfs_csr_launch(int n, int64_t max_deg, const int64_t *row_ptr, const int32_t *col, int32_t *order,
+                      int32_t *pos, int32_t *parent, void *ws, int num_sms, cudaStream_t stream);
+
+// ---- CSR check (peo_csr.cu)
+int peo_csr_launch(int n, const int64_t *row_ptr, const int32_t *col, const int32_t *order, const int32_t *pos,
+                   int32_t *parent, bool parent_known, unsigned long long *key, int num_sms, cudaStream_t stream);
+// flag (device int) receives an OR of layout violations, 0 when the CSR is well formed.
+int validate_csr_launch(int n, int64_t nnz, const int64_t *row_ptr, const int32_t *col, int *flag, int num_sms,
+                        cudaStream_t stream);
+
 }  // namespace cg

@@ -1,0 +1,120 @@
+// peo_csr.cu — perfect-elimination check of CSR graphs (Sections 5.3, 6.2).
+//
+// One warp per vertex v: p = p(v) (recorded by the CSR LexBFS, or computed
+// here for a caller's order as the neighbour with the largest order index
+// below pos(v)); then every neighbour u != p of v with pos(u) < pos(v) must be
+// in N(p), tested by binary search in p's sorted row.  Rows are sorted, so the
+// lowest violating u of v lies in the first 32-neighbour chunk that has one;
+// the first violating v in order wins the 64-bit atomicMin on
+// (pos(v) << 32 | u).  Also: a layout validator for CSR inputs.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace cg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ bool sorted_contains(const int32_t *__restrict__ a, int64_t len, int32_t key) {
+    int64_t lo = 0, hi = len;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < key) lo = mid + 1; else hi = mid;
+    }
+    return lo < len && __ldg(a + lo) == key;
+}
+
+template <bool PARENT_KNOWN>
+__global__ void __launch_bounds__(kThreads) peo_csr_kernel(int n, const int64_t *__restrict__ row_ptr,
+                                                           const int32_t *__restrict__ col,
+                                                           const int32_t *__restrict__ order,
+                                                           const int32_t *__restrict__ pos,
+                                                           int32_t *__restrict__ parent,
+                                                           unsigned long long *__restrict__ key) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t vv = warp; vv < n; vv += nwarps) {
+        const int v = (int)vv;
+        const int pv = __ldg(pos + v);
+        const int64_t b = __ldg(row_ptr + v), e = __ldg(row_ptr + v + 1);
+        int p;
+        if (PARENT_KNOWN) {
+            p = __ldg(parent + v);
+        } else {
+            int best = -1;
+            for (int64_t j = b + lane; j < e; j += 32) {
+                const int pu = __ldg(pos + __ldg(col + j));
+                if (pu < pv && pu > best) best = pu;
+            }
+            best = __reduce_max_sync(0xFFFFFFFFu, best);
+            p = best >= 0 ? __ldg(order + best) : -1;
+            if (lane == 0) parent[v] = p;
+        }
+        if (p < 0) continue;
+        const int64_t pb = __ldg(row_ptr + p), pe = __ldg(row_ptr + p + 1);
+        unsigned umin = 0xFFFFFFFFu;
+        for (int64_t j0 = b; j0 < e; j0 += 32) {
+            const int64_t j = j0 + lane;
+            if (j < e) {
+                const int u = __ldg(col + j);
+                if (u != p && __ldg(pos + u) < pv && !sorted_contains(col + pb, pe - pb, u)) umin = (unsigned)u;
+            }
+            umin = __reduce_min_sync(0xFFFFFFFFu, umin);
+            if (umin != 0xFFFFFFFFu) break;
+        }
+        if (lane == 0 && umin != 0xFFFFFFFFu) atomicMin(key, ((unsigned long long)(unsigned)pv << 32) | umin);
+    }
+}
+
+// flag bits: 1 row_ptr not monotone / wrong ends, 2 column out of range,
+// 4 row not strictly increasing, 8 self-loop, 16 edge without its reverse
+__global__ void validate_csr_kernel(int n, int64_t nnz, const int64_t *__restrict__ row_ptr,
+                                    const int32_t *__restrict__ col, int *flag) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = row_ptr[v], e = row_ptr[v + 1];
+        int bad = 0;
+        if (e < b || b < 0 || e > nnz || (v == 0 && b != 0) || (v == n - 1 && e != nnz)) {
+            atomicOr(flag, 1);
+            continue;
+        }
+        for (int64_t j = b; j < e; ++j) {
+            const int u = col[j];
+            if (u < 0 || u >= n) { bad |= 2; continue; }
+            if (j > b && col[j - 1] >= u) bad |= 4;
+            if (u == v) bad |= 8;
+            const int64_t ub = row_ptr[u], ue = row_ptr[u + 1];
+            if (ue >= ub && ub >= 0 && ue <= nnz && !sorted_contains(col + ub, ue - ub, (int32_t)v)) bad |= 16;
+        }
+        if (bad) atomicOr(flag, bad);
+    }
+}
+
+}  // namespace
+
+int peo_csr_launch(int n, const int64_t *row_ptr, const int32_t *col, const int32_t *order, const int32_t *pos,
+                   int32_t *parent, bool parent_known, unsigned long long *key, int num_sms, cudaStream_t stream) {
+    CG_CUDA_TRY(cudaMemsetAsync(key, 0xFF, sizeof(unsigned long long), stream));
+    if (n <= 0) return CG_OK;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kThreads / 32), (int64_t)num_sms * 8));
+    if (parent_known)
+        peo_csr_kernel<true><<<blocks, kThreads, 0, stream>>>(n, row_ptr, col, order, pos, parent, key);
+    else
+        peo_csr_kernel<false><<<blocks, kThreads, 0, stream>>>(n, row_ptr, col, order, pos, parent, key);
+    CG_LAUNCH_CHECK("peo_csr_kernel");
+    return CG_OK;
+}
+
+int validate_csr_launch(int n, int64_t nnz, const int64_t *row_ptr, const int32_t *col, int *flag, int num_sms,
+                        cudaStream_t stream) {
+    CG_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), stream));
+    if (n <= 0) return CG_OK;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms * 8));
+    validate_csr_kernel<<<blocks, 256, 0, stream>>>(n, nnz, row_ptr, col, flag);
+    CG_LAUNCH_CHECK("validate_csr_kernel");
+    return CG_OK;
+}
+
+}  // namespace cg
