@@ -198,19 +198,44 @@ int cg_chordal_test_dense_noalloc(const cg_dense *g, cg_result *res, int32_t *or
 
 /*
  * Per-phase timing (tracing aid; not part of the paper).  When enabled, each
- * call records CUDA events on its stream around the LexBFS launch and around
- * the check (check + finalize launches).  cg_profile_read waits for the
+ * call records CUDA events on the stream a phase runs on: around LexBFS
+ * launches, around the check (check + finalize), around fused one-CTA
+ * kernels, and around whole batch calls.  cg_profile_read waits for the
  * recorded events, returns the sums since the last read and resets them.
  */
 typedef struct {
-    double lexbfs_ms;        /* summed LexBFS kernel time */
-    double check_ms;         /* summed perfect-elimination check time */
+    double lexbfs_ms;        /* summed LexBFS-only kernel time (single graphs, large batch graphs) */
+    double check_ms;         /* summed perfect-elimination check time (check + finalize launches) */
+    double fused_ms;         /* summed time of one-CTA whole-test kernels (batch buckets) */
+    double batch_ms;         /* summed time of whole batch calls / batch plan runs */
     int64_t lexbfs_launches;
     int64_t check_launches;
+    int64_t fused_launches;
+    int64_t batch_calls;
     int64_t kernel_launches; /* all kernels this library launched since the last read */
 } cg_profile;
 
 int cg_profile_enable(cg_context *ctx, int enable);
+/* A batch as a reusable plan: the graphs' descriptors and the scratch are
+ * uploaded once and the whole launch sequence (size buckets on forked
+ * streams) is captured into a CUDA graph; each run replays it on `stream`.
+ * The plan records the caller's device pointers (rows, res, orders): they
+ * must stay valid, and their contents may change between runs.  Arguments as
+ * for cg_chordal_test_batch. */
+typedef struct cg_batch_plan cg_batch_plan;
+int cg_batch_plan_create(cg_context *ctx, const cg_dense *graphs, int32_t count, cg_result *res, int32_t *orders,
+                         const int64_t *order_offsets, cg_batch_plan **out);
+int cg_batch_plan_run(cg_batch_plan *plan, cudaStream_t stream);
+int cg_batch_plan_destroy(cg_batch_plan *plan);
+
+/* Autotuner of the batched path: for each size bucket of `graphs`
+ * (n <= 16, 32, ..., 4096) times the one-CTA kernel with 64, 128, 256 and
+ * 512 threads on `stream` (synchronising) and keeps the fastest in the
+ * context.  cg_autotune_get / _set read or restore the table (slots 0..8,
+ * 0 = size rule) so callers can persist it. */
+int cg_batch_autotune(cg_context *ctx, const cg_dense *graphs, int32_t count, cudaStream_t stream);
+int cg_autotune_get(cg_context *ctx, int32_t *threads, int32_t slots);
+int cg_autotune_set(cg_context *ctx, const int32_t *threads, int32_t slots);
 int cg_profile_read(cg_context *ctx, cg_profile *out);
 
 #ifdef __cplusplus

@@ -42,8 +42,10 @@ class cg_result(ctypes.Structure):
 
 
 class cg_profile(ctypes.Structure):
-    _fields_ = [("lexbfs_ms", ctypes.c_double), ("check_ms", ctypes.c_double), ("lexbfs_launches", ctypes.c_int64),
-                ("check_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+    _fields_ = [("lexbfs_ms", ctypes.c_double), ("check_ms", ctypes.c_double), ("fused_ms", ctypes.c_double),
+                ("batch_ms", ctypes.c_double), ("lexbfs_launches", ctypes.c_int64),
+                ("check_launches", ctypes.c_int64), ("fused_launches", ctypes.c_int64),
+                ("batch_calls", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
 
 
 class cg_config(ctypes.Structure):
@@ -72,6 +74,12 @@ SIGNATURES = {
     "cg_chordal_test_csr_host": ([P, I32, I64, P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_dense_noalloc": ([P, P, P, P], ctypes.c_int),
     "cg_profile_enable": ([P, I32], ctypes.c_int),
+    "cg_batch_plan_create": ([P, P, I32, P, P, P, P], ctypes.c_int),
+    "cg_batch_plan_run": ([P, P], ctypes.c_int),
+    "cg_batch_plan_destroy": ([P], ctypes.c_int),
+    "cg_batch_autotune": ([P, P, I32, P], ctypes.c_int),
+    "cg_autotune_get": ([P, P, I32], ctypes.c_int),
+    "cg_autotune_set": ([P, P, I32], ctypes.c_int),
     "cg_profile_read": ([P, P], ctypes.c_int),
 }
 
@@ -125,6 +133,12 @@ cg_chordal_test_csr = _fn("cg_chordal_test_csr")
 cg_chordal_test_csr_host = _fn("cg_chordal_test_csr_host")
 cg_chordal_test_dense_noalloc = _fn("cg_chordal_test_dense_noalloc")
 cg_profile_enable = _fn("cg_profile_enable")
+cg_batch_plan_create = _fn("cg_batch_plan_create")
+cg_batch_plan_run = _fn("cg_batch_plan_run")
+cg_batch_plan_destroy = _fn("cg_batch_plan_destroy")
+cg_batch_autotune = _fn("cg_batch_autotune")
+cg_autotune_get = _fn("cg_autotune_get")
+cg_autotune_set = _fn("cg_autotune_set")
 cg_profile_read = _fn("cg_profile_read")
 
 
@@ -263,3 +277,56 @@ def chordal_test_csr_host(ctx: Context, row_ptr, col, n: int, order_host=None, s
     _check(cg_chordal_test_csr_host(ctx.handle, n, nnz, hp(row_ptr), hp(col) if nnz else 0, ctypes.byref(out),
                                     hp(order_host), _stream(stream)))
     return out.astuple()
+
+
+def _dense_array(graphs):
+    arr = (cg_dense * max(len(graphs), 1))()
+    for k, (rows, n) in enumerate(graphs):
+        arr[k] = dense_desc(rows, n)
+    return arr
+
+
+class BatchPlan:
+    """A captured batch (cg_batch_plan): run() replays one CUDA graph."""
+
+    def __init__(self, ctx: Context, graphs, res, orders=None, order_offsets=None):
+        self.ctx = ctx
+        self._keep = (graphs, res, orders)
+        arr = _dense_array(graphs)
+        offs = None
+        if order_offsets is not None:
+            offs = (ctypes.c_int64 * max(len(graphs), 1))(*[int(x) for x in order_offsets])
+        h = ctypes.c_void_p()
+        _check(cg_batch_plan_create(ctx.handle, arr, len(graphs), _ptr(res), _ptr(orders), offs, ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(cg_batch_plan_run(self.handle, _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            _check(cg_batch_plan_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_autotune(ctx: Context, graphs, stream=None) -> list:
+    arr = _dense_array(graphs)
+    _check(cg_batch_autotune(ctx.handle, arr, len(graphs), _stream(stream)))
+    return autotune_get(ctx)
+
+
+def autotune_get(ctx: Context) -> list:
+    buf = (ctypes.c_int32 * 9)()
+    _check(cg_autotune_get(ctx.handle, buf, 9))
+    return list(buf)
+
+
+def autotune_set(ctx: Context, table) -> None:
+    buf = (ctypes.c_int32 * 9)(*[int(x) for x in table][:9])
+    _check(cg_autotune_set(ctx.handle, buf, 9))

@@ -36,10 +36,16 @@ struct cg_context {
     size_t pinned_bytes = 0;
     cudaEvent_t staged{};        // recorded after each staging upload
     bool staged_pending = false;
+    // concurrent size buckets of a batch: forked streams and join events
+    static constexpr int kAux = 8;
+    static constexpr int kBuckets = 10;          // n in (2^(b+3), 2^(b+4)] for b < 9, then n > 4096
+    cudaStream_t aux[kAux]{};
+    cudaEvent_t fork{}, join[kBuckets]{};
+    int tuned_threads[kBuckets]{};               // 0 = size rule
     // per-phase timing
     bool profiling = false;
     std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_lex, ev_check;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_lex, ev_check, ev_fused, ev_batch;
     int64_t launches = 0;
 };
 
@@ -162,14 +168,190 @@ int check_csr(const cg_csr *g) {
     return CG_OK;
 }
 
-DenseDesc desc_of(const cg_dense *g, int64_t vbase, int64_t obase) {
-    DenseDesc d;
+DenseDesc desc_of(const cg_dense *g, int64_t vbase, int64_t obase, int32_t rindex = 0) {
+    DenseDesc d{};
     d.rows = g->rows;
     d.n = g->n;
     d.words = g->words_per_row;
     d.vbase = vbase;
     d.obase = obase;
+    d.rindex = rindex;
     return d;
+}
+
+// ---------------------------------------------------------------- batches
+// Graphs are grouped into size buckets (b < 9: n in (2^(b+3), 2^(b+4)], i.e.
+// up to 16, 32, ..., 4096; b = 9: n > 4096).  Buckets 0..8 run the fused
+// one-CTA test; bucket 9 runs the per-graph LexBFS CTA plus the grid-wide
+// check.  Within a bucket graphs are sorted largest first, and CTAs take
+// them from an atomic counter (longest job first).
+int bucket_of(int n) {
+    if (n > kFusedMaxN) return 9;
+    int b = 0;
+    while (b < 8 && n > (16 << b)) ++b;
+    return b;
+}
+
+struct BatchLayout {
+    struct Bucket {
+        int begin = 0, end = 0, nmax = 0;
+        FusedPlan fplan{};
+        LexPlan lplan{};
+        int ctas = 0;
+        int64_t vbegin = 0, vend = 0;   // packed vertex range (bucket 9)
+    };
+    int count = 0;
+    std::vector<DenseDesc> descs;      // bucket order
+    std::vector<int64_t> voff;         // packed vertex offset of each desc (+ total)
+    Bucket bk[cg_context::kBuckets];
+    int64_t total = 0;
+};
+
+int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const int64_t *order_offsets,
+                BatchLayout *L) {
+    int rc;
+    L->count = count;
+    std::vector<int> idx(count);
+    std::vector<int> bucket(count);
+    for (int k = 0; k < count; ++k) {
+        if ((rc = check_dense(&graphs[k]))) return set_error(rc, "graph %d: %s", k, cg_last_error_string());
+        if (order_offsets && order_offsets[k] < 0) return set_error(CG_EINVAL, "graph %d: negative order offset", k);
+        idx[k] = k;
+        bucket[k] = bucket_of(graphs[k].n);
+    }
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        if (bucket[a] != bucket[b]) return bucket[a] < bucket[b];
+        return graphs[a].n > graphs[b].n;
+    });
+    L->descs.resize(count);
+    L->voff.resize(count + 1);
+    int64_t packed = 0, total = 0;
+    // packed order offsets follow input order when the caller gives none
+    std::vector<int64_t> obase(count);
+    for (int k = 0; k < count; ++k) {
+        obase[k] = order_offsets ? order_offsets[k] : packed;
+        packed += graphs[k].n;
+    }
+    for (int b = 0; b < cg_context::kBuckets; ++b) L->bk[b] = BatchLayout::Bucket{};
+    for (int j = 0; j < count; ++j) {
+        const int k = idx[j];
+        L->voff[j] = total;
+        L->descs[j] = desc_of(&graphs[k], total, obase[k], k);
+        total += graphs[k].n;
+    }
+    L->voff[count] = total;
+    L->total = total;
+    int j = 0;
+    for (int b = 0; b < cg_context::kBuckets; ++b) {
+        auto &B = L->bk[b];
+        B.begin = j;
+        while (j < count && bucket[idx[j]] == b) ++j;
+        B.end = j;
+        if (B.end == B.begin) continue;
+        B.nmax = graphs[idx[B.begin]].n;
+        B.vbegin = L->voff[B.begin];
+        B.vend = L->voff[B.end];
+        const int cnt = B.end - B.begin;
+        if (b < 9) {
+            if ((rc = fused_dense_plan(B.nmax, ctx->tuned_threads[b], &B.fplan))) return rc;
+            B.ctas = std::min(cnt, ctx->num_sms * fused_ctas_per_sm(B.fplan));
+        } else {
+            if ((rc = lexbfs_dense_plan(B.nmax, ctx->cfg.threads_override, &B.lplan))) return rc;
+            const int by_smem =
+                B.lplan.smem_bytes ? (int)std::max<size_t>(1, (228 * 1024) / (B.lplan.smem_bytes + 1024)) : 32;
+            const int by_threads = std::max(1, 2048 / B.lplan.threads);
+            B.ctas = std::max(1, std::min(cnt, ctx->num_sms * std::min(by_smem, by_threads)));
+        }
+    }
+    return CG_OK;
+}
+
+// Device buffers a batch needs (offsets into one allocation).
+struct BatchBuffers {
+    size_t o_desc, o_voff, o_order, o_pos, o_parent, o_keys, o_counter, o_gstate, bytes;
+};
+
+BatchBuffers batch_buffers(const BatchLayout &L, bool need_order) {
+    Carve cv;
+    BatchBuffers bb{};
+    bb.o_desc = cv.take<DenseDesc>(L.count);
+    bb.o_voff = cv.take<int64_t>(L.count + 1);
+    bb.o_order = cv.take<int32_t>(need_order ? L.total : 0);
+    bb.o_pos = cv.take<int32_t>(L.total);
+    bb.o_parent = cv.take<int32_t>(L.total);
+    bb.o_keys = cv.take<unsigned long long>(L.count);
+    bb.o_counter = cv.take<int>(cg_context::kBuckets * 64);
+    const auto &B9 = L.bk[9];
+    bb.o_gstate = cv.take<unsigned char>(B9.end > B9.begin && B9.lplan.wide_ids ? B9.lplan.gstate_bytes * B9.ctas : 0);
+    bb.bytes = cv.off;
+    return bb;
+}
+
+// Enqueues every bucket on the context's forked streams and joins them back
+// into `stream`.  base: device allocation laid out by batch_buffers (the
+// descriptors and offsets must already be there).
+int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb, unsigned char *base,
+                  int32_t *orders, cg_result *res, cudaStream_t stream) {
+    int rc;
+    auto P = [&](size_t off) { return base + off; };
+    const DenseDesc *ddesc = reinterpret_cast<const DenseDesc *>(P(bb.o_desc));
+    const int64_t *dvoff = reinterpret_cast<const int64_t *>(P(bb.o_voff));
+    int32_t *order = orders ? orders : reinterpret_cast<int32_t *>(P(bb.o_order));
+    int32_t *pos = reinterpret_cast<int32_t *>(P(bb.o_pos));
+    int32_t *parent = reinterpret_cast<int32_t *>(P(bb.o_parent));
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(P(bb.o_keys));
+    int *counters = reinterpret_cast<int *>(P(bb.o_counter));
+    CG_CUDA_TRY(cudaEventRecord(ctx->fork, stream));
+    int used = 0;
+    for (int b = 0; b < cg_context::kBuckets; ++b) {
+        const auto &B = L.bk[b];
+        const int cnt = B.end - B.begin;
+        if (cnt <= 0) continue;
+        cudaStream_t s = ctx->aux[used % cg_context::kAux];
+        CG_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fork, 0));
+        if (b < 9) {
+            PhaseTimer pt(ctx, &ctx->ev_fused, s);
+            if ((rc = fused_dense_launch(B.fplan, ddesc + B.begin, cnt, B.ctas, order, pos, parent, res,
+                                         counters + 64 * b, s)))
+                return rc;
+            ctx->launches += 1;
+        } else {
+            {
+                PhaseTimer pt(ctx, &ctx->ev_lex, s);
+                if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, parent,
+                                              B.lplan.wide_ids ? P(bb.o_gstate) : nullptr, counters + 64 * b, s)))
+                    return rc;
+            }
+            PhaseTimer pt(ctx, &ctx->ev_check, s);
+            // the check over this bucket's vertices (a slice of the offset table)
+            if ((rc = peo_dense_launch(ddesc + B.begin, DenseDesc{}, cnt, dvoff + B.begin, B.vend - B.vbegin, order,
+                                       pos, parent, true, keys + B.begin, ctx->num_sms, s)))
+                return rc;
+            if ((rc = finalize_launch(ddesc + B.begin, DenseDesc{}, cnt, keys + B.begin, order, parent, res, s)))
+                return rc;
+            ctx->launches += 3;
+        }
+        CG_CUDA_TRY(cudaEventRecord(ctx->join[b], s));
+        CG_CUDA_TRY(cudaStreamWaitEvent(stream, ctx->join[b], 0));
+        ++used;
+    }
+    return CG_OK;
+}
+
+int upload_layout(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb, unsigned char *base,
+                  cudaStream_t stream) {
+    int rc;
+    const size_t bytes_desc = sizeof(DenseDesc) * L.count, bytes_voff = sizeof(int64_t) * (L.count + 1);
+    if ((rc = ensure_pinned(ctx, align_up(bytes_desc, 16) + bytes_voff + 64))) return rc;
+    unsigned char *hp = static_cast<unsigned char *>(ctx->pinned);
+    std::memcpy(hp, L.descs.data(), bytes_desc);
+    std::memcpy(hp + align_up(bytes_desc, 16), L.voff.data(), bytes_voff);
+    CG_CUDA_TRY(cudaMemcpyAsync(base + bb.o_desc, hp, bytes_desc, cudaMemcpyHostToDevice, stream));
+    CG_CUDA_TRY(cudaMemcpyAsync(base + bb.o_voff, hp + align_up(bytes_desc, 16), bytes_voff, cudaMemcpyHostToDevice,
+                                stream));
+    CG_CUDA_TRY(cudaEventRecord(ctx->staged, stream));
+    ctx->staged_pending = true;
+    return CG_OK;
 }
 
 // LexBFS and (optionally) the check for one graph given by value.
@@ -276,6 +458,11 @@ int cg_context_create(const cg_config *cfg, cg_context **out) {
     cudaError_t e = cudaSetDevice(ctx->cfg.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->cfg.device);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
+    for (int i = 0; e == cudaSuccess && i < cg_context::kBuckets; ++i)
+        e = cudaEventCreateWithFlags(&ctx->join[i], cudaEventDisableTiming);
+    for (int i = 0; e == cudaSuccess && i < cg_context::kAux; ++i)
+        e = cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete ctx;
         return set_error(CG_ECUDA, "context creation on device %d failed: %s", cfg ? cfg->device : 0,
@@ -297,8 +484,12 @@ int cg_profile_read(cg_context *ctx, cg_profile *out) {
     if ((rc = check_ctx(ctx))) return rc;
     if (!out) return set_error(CG_EINVAL, "null profile pointer");
     cg_profile p{};
-    for (int phase = 0; phase < 2; ++phase) {
-        auto &list = phase == 0 ? ctx->ev_lex : ctx->ev_check;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *lists[4] = {&ctx->ev_lex, &ctx->ev_check, &ctx->ev_fused,
+                                                                  &ctx->ev_batch};
+    double *sums[4] = {&p.lexbfs_ms, &p.check_ms, &p.fused_ms, &p.batch_ms};
+    int64_t *counts[4] = {&p.lexbfs_launches, &p.check_launches, &p.fused_launches, &p.batch_calls};
+    for (int phase = 0; phase < 4; ++phase) {
+        auto &list = *lists[phase];
         double sum = 0;
         for (auto &ab : list) {
             CG_CUDA_TRY(cudaEventSynchronize(ab.second));
@@ -308,8 +499,8 @@ int cg_profile_read(cg_context *ctx, cg_profile *out) {
             ctx->ev_free.push_back(ab.first);
             ctx->ev_free.push_back(ab.second);
         }
-        (phase == 0 ? p.lexbfs_ms : p.check_ms) = sum;
-        (phase == 0 ? p.lexbfs_launches : p.check_launches) = (int64_t)list.size();
+        *sums[phase] = sum;
+        *counts[phase] = (int64_t)list.size();
         list.clear();
     }
     p.kernel_launches = ctx->launches;
@@ -322,12 +513,15 @@ int cg_context_destroy(cg_context *ctx) {
     if (!ctx) return CG_OK;
     cudaSetDevice(ctx->cfg.device);
     cudaDeviceSynchronize();
-    for (auto &ab : ctx->ev_lex) { cudaEventDestroy(ab.first); cudaEventDestroy(ab.second); }
-    for (auto &ab : ctx->ev_check) { cudaEventDestroy(ab.first); cudaEventDestroy(ab.second); }
+    for (auto *l : {&ctx->ev_lex, &ctx->ev_check, &ctx->ev_fused, &ctx->ev_batch})
+        for (auto &ab : *l) { cudaEventDestroy(ab.first); cudaEventDestroy(ab.second); }
     for (auto e : ctx->ev_free) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     cudaEventDestroy(ctx->staged);
+    cudaEventDestroy(ctx->fork);
+    for (int i = 0; i < cg_context::kBuckets; ++i) cudaEventDestroy(ctx->join[i]);
+    for (int i = 0; i < cg_context::kAux; ++i) cudaStreamDestroy(ctx->aux[i]);
     delete ctx;
     return CG_OK;
 }
@@ -488,68 +682,179 @@ int cg_chordal_test_batch(cg_context *ctx, const cg_dense *graphs, int32_t count
     if (count < 0) return set_error(CG_EINVAL, "count must be >= 0");
     if (count == 0) return CG_OK;
     if (!graphs || !res) return set_error(CG_EINVAL, "null graphs or result pointer");
-    std::vector<DenseDesc> descs(count);
-    std::vector<int64_t> voff(count + 1);
-    int64_t total = 0;
-    int n_max = 0;
-    for (int k = 0; k < count; ++k) {
-        if ((rc = check_dense(&graphs[k]))) return set_error(rc, "graph %d: %s", k, cg_last_error_string());
-        voff[k] = total;
-        const int64_t ob = order_offsets ? order_offsets[k] : total;
-        if (ob < 0) return set_error(CG_EINVAL, "graph %d: negative order offset", k);
-        descs[k] = desc_of(&graphs[k], total, ob);
-        total += graphs[k].n;
-        n_max = std::max(n_max, graphs[k].n);
+    BatchLayout L;
+    if ((rc = make_layout(ctx, graphs, count, order_offsets, &L))) return rc;
+    const BatchBuffers bb = batch_buffers(L, orders == nullptr);
+    if ((rc = ensure_ws(ctx, bb.bytes))) return rc;
+    unsigned char *base = static_cast<unsigned char *>(ctx->ws);
+    if ((rc = upload_layout(ctx, L, bb, base, stream))) return rc;
+    PhaseTimer pt(ctx, &ctx->ev_batch, stream);
+    return enqueue_batch(ctx, L, bb, base, orders, res, stream);
+}
+
+struct cg_batch_plan {
+    cg_context *ctx = nullptr;
+    void *mem = nullptr;
+    cudaGraph_t graph{};
+    cudaGraphExec_t exec{};
+    int64_t launches = 0;
+};
+
+int cg_batch_plan_create(cg_context *ctx, const cg_dense *graphs, int32_t count, cg_result *res, int32_t *orders,
+                         const int64_t *order_offsets, cg_batch_plan **out) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (!out) return set_error(CG_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (count <= 0 || !graphs || !res) return set_error(CG_EINVAL, "a plan needs count > 0, graphs and res");
+    BatchLayout L;
+    if ((rc = make_layout(ctx, graphs, count, order_offsets, &L))) return rc;
+    const BatchBuffers bb = batch_buffers(L, orders == nullptr);
+    cg_batch_plan *plan = new (std::nothrow) cg_batch_plan();
+    if (!plan) return set_error(CG_ENOMEM, "plan allocation failed");
+    plan->ctx = ctx;
+    if (cudaMalloc(&plan->mem, bb.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete plan;
+        return set_error(CG_ENOMEM, "plan buffers (%zu bytes) allocation failed", bb.bytes);
     }
-    voff[count] = total;
-    LexPlan plan;
-    if ((rc = lexbfs_dense_plan(n_max, ctx->cfg.threads_override, &plan))) return rc;
-    // resident CTAs: shared memory and threads per SM bound the co-resident count
-    const int by_smem = plan.smem_bytes ? (int)std::max<size_t>(1, (228 * 1024) / (plan.smem_bytes + 1024)) : 32;
-    const int by_threads = std::max(1, 2048 / plan.threads);
-    const int ctas = std::max(1, std::min(count, ctx->num_sms * std::min(by_smem, by_threads)));
-    Carve cv;
-    const size_t o_desc = cv.take<DenseDesc>(count);
-    const size_t o_voff = cv.take<int64_t>(count + 1);
-    const size_t o_order = cv.take<int32_t>(orders ? 0 : total);
-    const size_t o_pos = cv.take<int32_t>(total);
-    const size_t o_parent = cv.take<int32_t>(total);
-    const size_t o_keys = cv.take<unsigned long long>(count);
-    const size_t o_counter = cv.take<int>(1);
-    const size_t o_gstate = cv.take<unsigned char>(plan.wide_ids ? plan.gstate_bytes * (size_t)ctas : 0);
-    if ((rc = ensure_ws(ctx, cv.off))) return rc;
-    // stage descriptors + offsets in pinned memory, one upload
-    const size_t bytes_desc = sizeof(DenseDesc) * count, bytes_voff = sizeof(int64_t) * (count + 1);
-    if ((rc = ensure_pinned(ctx, bytes_desc + bytes_voff + 64))) return rc;
-    unsigned char *hp = static_cast<unsigned char *>(ctx->pinned);
-    std::memcpy(hp, descs.data(), bytes_desc);
-    std::memcpy(hp + align_up(bytes_desc, 16), voff.data(), bytes_voff);
-    CG_CUDA_TRY(cudaMemcpyAsync(at<void>(ctx, o_desc), hp, bytes_desc, cudaMemcpyHostToDevice, stream));
-    CG_CUDA_TRY(cudaMemcpyAsync(at<void>(ctx, o_voff), hp + align_up(bytes_desc, 16), bytes_voff,
-                                cudaMemcpyHostToDevice, stream));
-    CG_CUDA_TRY(cudaEventRecord(ctx->staged, stream));
-    ctx->staged_pending = true;
-    const DenseDesc *ddesc = at<DenseDesc>(ctx, o_desc);
-    const int64_t *dvoff = at<int64_t>(ctx, o_voff);
-    int32_t *order = orders ? orders : at<int32_t>(ctx, o_order);
-    int32_t *pos = at<int32_t>(ctx, o_pos);
-    int32_t *parent = at<int32_t>(ctx, o_parent);
-    unsigned long long *keys = at<unsigned long long>(ctx, o_keys);
-    const DenseDesc none{};
-    {
-        PhaseTimer pt(ctx, &ctx->ev_lex, stream);
-        if ((rc = lexbfs_dense_launch(plan, ddesc, none, count, ctas, order, pos, parent,
-                                      plan.wide_ids ? at<void>(ctx, o_gstate) : nullptr, at<int>(ctx, o_counter),
-                                      stream)))
-            return rc;
-        ctx->launches += 1;
+    unsigned char *base = static_cast<unsigned char *>(plan->mem);
+    cudaStream_t cs = ctx->aux[cg_context::kAux - 1];
+    rc = upload_layout(ctx, L, bb, base, cs);
+    if (rc == CG_OK) {
+        cudaError_t e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) rc = set_error(CG_ECUDA, "plan upload failed: %s", cudaGetErrorString(e));
     }
-    PhaseTimer pt(ctx, &ctx->ev_check, stream);
-    if ((rc = peo_dense_launch(ddesc, none, count, dvoff, total, order, pos, parent, true, keys, ctx->num_sms,
-                               stream)))
+    // capture the launch sequence once; runs replay it
+    cudaStream_t origin = nullptr;
+    if (rc == CG_OK && cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess)
+        rc = set_error(CG_ECUDA, "stream creation failed");
+    if (rc == CG_OK) {
+        const int64_t before = ctx->launches;
+        const bool prof = ctx->profiling;
+        ctx->profiling = false;   // no timing events inside the captured graph
+        cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) rc = set_error(CG_ECUDA, "begin capture failed: %s", cudaGetErrorString(e));
+        if (rc == CG_OK) {
+            const int erc = enqueue_batch(ctx, L, bb, base, orders, res, origin);
+            e = cudaStreamEndCapture(origin, &plan->graph);
+            if (erc) rc = erc;
+            else if (e != cudaSuccess) rc = set_error(CG_ECUDA, "end capture failed: %s", cudaGetErrorString(e));
+        }
+        plan->launches = ctx->launches - before;
+        ctx->launches = before;
+        ctx->profiling = prof;
+        if (rc == CG_OK && cudaGraphInstantiate(&plan->exec, plan->graph, 0) != cudaSuccess)
+            rc = set_error(CG_ECUDA, "graph instantiation failed");
+    }
+    if (origin) cudaStreamDestroy(origin);
+    if (rc) {
+        cudaGetLastError();
+        if (plan->exec) cudaGraphExecDestroy(plan->exec);
+        if (plan->graph) cudaGraphDestroy(plan->graph);
+        cudaFree(plan->mem);
+        delete plan;
         return rc;
-    ctx->launches += total > 0 ? 2 : 1;
-    return finalize_launch(ddesc, none, count, keys, order, parent, res, stream);
+    }
+    *out = plan;
+    return CG_OK;
+}
+
+int cg_batch_plan_run(cg_batch_plan *plan, cudaStream_t stream) {
+    if (!plan) return set_error(CG_EINVAL, "null plan");
+    int rc;
+    if ((rc = check_ctx(plan->ctx))) return rc;
+    PhaseTimer pt(plan->ctx, &plan->ctx->ev_batch, stream);
+    CG_CUDA_TRY(cudaGraphLaunch(plan->exec, stream));
+    plan->ctx->launches += plan->launches;
+    return CG_OK;
+}
+
+int cg_batch_plan_destroy(cg_batch_plan *plan) {
+    if (!plan) return CG_OK;
+    cudaSetDevice(plan->ctx->cfg.device);
+    cudaDeviceSynchronize();
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->mem) cudaFree(plan->mem);
+    delete plan;
+    return CG_OK;
+}
+
+int cg_batch_autotune(cg_context *ctx, const cg_dense *graphs, int32_t count, cudaStream_t stream) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (count <= 0 || !graphs) return set_error(CG_EINVAL, "autotune needs graphs");
+    // time each fused bucket alone with each CTA size; keep the fastest
+    Carve cv;
+    const size_t o_res = cv.take<cg_result>(count);
+    const size_t o_rest = cv.take<unsigned char>(0);
+    (void)o_rest;
+    BatchLayout L0;
+    if ((rc = make_layout(ctx, graphs, count, nullptr, &L0))) return rc;
+    const BatchBuffers bb0 = batch_buffers(L0, true);
+    if ((rc = ensure_ws(ctx, cv.off + bb0.bytes + kAlign))) return rc;
+    cg_result *res = at<cg_result>(ctx, o_res);
+    unsigned char *base = static_cast<unsigned char *>(ctx->ws) + align_up(cv.off, kAlign);
+    cudaEvent_t a, b;
+    CG_CUDA_TRY(cudaEventCreate(&a));
+    CG_CUDA_TRY(cudaEventCreate(&b));
+    const int cands[4] = {64, 128, 256, 512};
+    for (int bk = 0; bk < 9; ++bk) {
+        const auto &B0 = L0.bk[bk];
+        if (B0.end <= B0.begin) continue;
+        float best = 1e30f;
+        int best_t = 0;
+        for (int c : cands) {
+            ctx->tuned_threads[bk] = c;
+            BatchLayout L;
+            if (make_layout(ctx, graphs, count, nullptr, &L) != CG_OK) { cudaGetLastError(); continue; }
+            const BatchBuffers bb = batch_buffers(L, true);
+            if ((rc = upload_layout(ctx, L, bb, base, stream))) break;
+            const auto &B = L.bk[bk];
+            int32_t *order = reinterpret_cast<int32_t *>(base + bb.o_order);
+            int32_t *pos = reinterpret_cast<int32_t *>(base + bb.o_pos);
+            int32_t *parent = reinterpret_cast<int32_t *>(base + bb.o_parent);
+            const DenseDesc *dd = reinterpret_cast<const DenseDesc *>(base + bb.o_desc);
+            int *ctr = reinterpret_cast<int *>(base + bb.o_counter);
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rc == CG_OK; ++rep) {   // second run is timed
+                cudaEventRecord(a, stream);
+                rc = fused_dense_launch(B.fplan, dd + B.begin, B.end - B.begin, B.ctas, order, pos, parent, res, ctr,
+                                        stream);
+                cudaEventRecord(b, stream);
+                cudaEventSynchronize(b);
+                cudaEventElapsedTime(&ms, a, b);
+            }
+            if (rc) break;
+            if (ms < best) {
+                best = ms;
+                best_t = c;
+            }
+        }
+        ctx->tuned_threads[bk] = best_t;
+        if (rc) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc;
+}
+
+int cg_autotune_get(cg_context *ctx, int32_t *threads, int32_t slots) {
+    if (!ctx || !threads) return set_error(CG_EINVAL, "null argument");
+    for (int i = 0; i < slots && i < cg_context::kBuckets; ++i) threads[i] = ctx->tuned_threads[i];
+    return CG_OK;
+}
+
+int cg_autotune_set(cg_context *ctx, const int32_t *threads, int32_t slots) {
+    if (!ctx || !threads) return set_error(CG_EINVAL, "null argument");
+    for (int i = 0; i < slots && i < cg_context::kBuckets; ++i) {
+        const int t = threads[i];
+        if (i < 9 && t != 0 && t != 64 && t != 128 && t != 256 && t != 512)
+            return set_error(CG_EINVAL, "bucket %d: CTA size %d not in {0, 64, 128, 256, 512}", i, t);
+        if (i < 9) ctx->tuned_threads[i] = t;
+    }
+    return CG_OK;
 }
 
 }  // extern "C"

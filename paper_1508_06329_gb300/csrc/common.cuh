@@ -35,6 +35,8 @@ struct DenseDesc {
     int32_t words;
     int64_t vbase;          // offset of this graph's vertices in the packed pos / parent workspace
     int64_t obase;          // offset of this graph's order in the caller's order array
+    int32_t rindex;         // slot of this graph's result
+    int32_t pad;
 };
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

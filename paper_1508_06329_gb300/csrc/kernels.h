@@ -44,6 +44,20 @@ int invert_order_launch(const DenseDesc *descs, DenseDesc single, int count, con
 int finalize_launch(const DenseDesc *descs, DenseDesc single, int count, const unsigned long long *keys,
                     const int32_t *order, const int32_t *parent, cg_result *res, cudaStream_t stream);
 
+// ---- fused small-graph test, one CTA per graph (batch_dense.cu)
+constexpr int kFusedMaxN = 4096;
+constexpr size_t kFusedSmemLimit = 227 * 1024 - 64;
+struct FusedPlan {
+    int threads;
+    bool rows_smem;
+    size_t smem_bytes;
+};
+// threads = 0 picks by size; otherwise 64, 128, 256 or 512.
+int fused_dense_plan(int n_max, int threads, FusedPlan *plan);
+int fused_dense_launch(const FusedPlan &plan, const DenseDesc *descs, int count, int ctas, int32_t *order,
+                       int32_t *pos, int32_t *parent, cg_result *res, int *work_counter, cudaStream_t stream);
+int fused_ctas_per_sm(const FusedPlan &plan);
+
 // ---- CSR LexBFS (lexbfs_csr.cu): one warp per graph, state in `ws`
 size_t lexbfs_csr_workspace_bytes(int64_t n, int64_t max_deg);
 int lexbfs_csr_launch(int n, int64_t max_deg, const int64_t *row_ptr, const int32_t *col, int32_t *order,

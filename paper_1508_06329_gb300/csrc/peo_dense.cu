@@ -34,7 +34,9 @@ __global__ void __launch_bounds__(kPeoThreads) peo_dense_kernel(const DenseDesc 
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t gv = warp; gv < total; gv += nwarps) {
+    const int64_t vbase0 = descs ? __ldg(voff) : 0;   // voff may be a slice of a larger offset table
+    for (int64_t gr = warp; gr < total; gr += nwarps) {
+        const int64_t gv = gr + vbase0;
         int gi = 0;
         if (descs) {
             int lo = 0, hi = count;
@@ -131,14 +133,16 @@ __global__ void finalize_kernel(const DenseDesc *__restrict__ descs, DenseDesc s
         r.p = parent[d.vbase + r.v];
         r.u = (int)(k & 0xFFFFFFFFu);
     }
-    res[gi] = r;
+    res[descs ? d.rindex : gi] = r;
 }
 
 __global__ void invert_order_kernel(const DenseDesc *__restrict__ descs, DenseDesc single, int count,
                                     const int64_t *__restrict__ voff, int64_t total,
                                     const int32_t *__restrict__ order, int32_t *__restrict__ pos) {
-    for (int64_t gv = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gv < total;
-         gv += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t vbase0 = descs ? __ldg(voff) : 0;
+    for (int64_t gr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gr < total;
+         gr += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t gv = gr + vbase0;
         int gi = 0;
         if (descs) {
             int lo = 0, hi = count;

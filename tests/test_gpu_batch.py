@@ -73,3 +73,44 @@ def test_batch_workload_full(ctx):
     graphs = gg.batch_dense(4096)
     res, orders = run_batch(ctx, graphs)
     check(graphs, res, orders)
+
+
+def test_batch_mixed_with_large_graphs(ctx):
+    """Size buckets 0..8 (one-CTA kernel) and 9 (n > 4096: LexBFS CTA + grid check)
+    in one call, results in input order."""
+    graphs = [gg.subtree_dense(5000, 700, 1), gg.cycle(5), gg.subtree_dense(300, 50, 2),
+              gg.plant_cycle(gg.subtree_dense(6000, 900, 3), 6, 3)[0], gg.empty_dense(0), gg.clique(17),
+              gg.subtree_dense(4096, 600, 4), gg.subtree_dense(4097, 600, 5)]
+    res, orders = run_batch(ctx, graphs)
+    check(graphs, res, orders)
+
+
+def test_batch_plan_replays(ctx):
+    graphs = gg.batch_dense(200, seed=77) + [gg.subtree_dense(5000, 800, 9)]
+    tens = [to_dev(g) for g in graphs]
+    res = torch.full((len(graphs), 4), -7, dtype=torch.int32, device=DEV)
+    orders = torch.full((sum(g.n for g in graphs),), -7, dtype=torch.int32, device=DEV)
+    plan = B.BatchPlan(ctx, [(t, g.n) for t, g in zip(tens, graphs)], res, orders)
+    for _ in range(2):
+        res.fill_(-7)
+        orders.fill_(-7)
+        plan.run()
+        torch.cuda.synchronize()
+        check(graphs, res.cpu().numpy(), orders.cpu().numpy())
+    # inputs may change between runs: planted cycles appear in the results
+    h, _ = gg.plant_cycle(graphs[0], 5, 1)
+    tens[0].copy_(to_dev(h))
+    plan.run()
+    torch.cuda.synchronize()
+    assert tuple(res[0].cpu().tolist()) == oracle.chordal_test(h).witness
+    plan.close()
+
+
+def test_autotune_keeps_results(ctx):
+    graphs = gg.batch_dense(300, seed=31)
+    table = B.batch_autotune(ctx, [(to_dev(g), g.n) for g in graphs])
+    assert len(table) == 9 and all(t in (0, 64, 128, 256, 512) for t in table)
+    res, orders = run_batch(ctx, graphs)
+    check(graphs, res, orders)
+    B.autotune_set(ctx, [0] * 9)
+    assert B.autotune_get(ctx) == [0] * 9
