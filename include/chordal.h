@@ -32,7 +32,9 @@
  *     context and grown on demand (device memory, plus pinned host staging).
  *   - Every call returns a cg_status.  On CG_ECUDA / CG_EINVAL,
  *     cg_last_error_string() describes the failure (thread-local).
- *   - A context may be used by one host thread at a time.
+ *   - A context may be used by one host thread at a time, and its workspace is
+ *     shared by its calls: calls whose GPU work may overlap (different streams)
+ *     need different contexts.
  */
 #ifndef CHORDAL_GB300_H
 #define CHORDAL_GB300_H
