@@ -66,6 +66,8 @@ def _load():
             lib.gg_peo_edges.restype = i64
             lib.gg_close_cycles_csr.argtypes = [i32, P, P, i32, u64, i32, P]
             lib.gg_stream.argtypes = [u64, P, i64]
+            lib.gg_dense_to_csr.argtypes = [i32, i32, P, P, P]
+            lib.gg_dense_to_csr.restype = i64
             _lib = lib
     return _lib
 
@@ -157,6 +159,13 @@ def csr_from_edges(n: int, eu: np.ndarray, ev: np.ndarray) -> CsrGraph:
 
 def dense_to_csr(g: DenseGraph) -> CsrGraph:
     n = g.n
+    if n > 4096:   # large graphs: C pass (no n x n byte matrix)
+        rows = np.ascontiguousarray(g.rows)
+        rp = np.zeros(n + 1, dtype=np.int64)
+        nnz = _load().gg_dense_to_csr(n, g.words, _ptr(rows), _ptr(rp), None)
+        col = np.empty(max(nnz, 1), dtype=np.int32)
+        _load().gg_dense_to_csr(n, g.words, _ptr(rows), _ptr(rp), _ptr(col))
+        return CsrGraph(n, rp, col[:nnz])
     if n == 0:
         return CsrGraph(0, np.zeros(1, np.int64), np.zeros(0, np.int32))
     bits = np.unpackbits(g.rows.view(np.uint8).reshape(n, -1), axis=1, bitorder="little")[:, :n]
@@ -377,3 +386,28 @@ def batch_dense(count: int = 4096, seed: int = SEED_BASE + 4, nmin: int = 16, nm
                 g, _ = plant_cycle(g, k, seed + 37 * i + 1)
         graphs.append(g)
     return graphs
+
+
+def serve_pool(count: int = 64, seed: int = SEED_BASE + 5, nmin: int = 64, nmax: int = 65536,
+               dense_below: int = 8192):
+    """Serving pool: N log-uniform in [nmin, nmax], target edge density
+    U[0.01, 0.2] (subtree model with about 56 / density tree nodes), half of
+    the graphs with a planted induced C_k (k ~ U{5..8}); graphs with
+    N < dense_below stay dense bit rows, larger ones are returned as CSR.
+    Returns a list of (graph, info)."""
+    u = _u01(seed, 3 * count)
+    ns = log_uniform_int(u[:count], nmin, nmax)
+    dens = 0.01 + 0.19 * u[count:2 * count]
+    out = []
+    for i in range(count):
+        n = int(ns[i])
+        t = max(2, int(round(56.0 / dens[i])))
+        g = subtree_dense(n, t, seed * 31 + i)
+        planted = i % 2 == 1
+        if planted:
+            k = 5 + int(rng_stream(seed + 97 * i, 1)[0] % np.uint64(4))
+            if n >= k:
+                g, _ = plant_cycle(g, k, seed + 101 * i)
+        info = {"n": n, "target_density": float(dens[i]), "tree_nodes": t, "planted": planted}
+        out.append((g if n < dense_below else dense_to_csr(g), info))
+    return out

@@ -385,3 +385,28 @@ int gg_close_cycles_csr(int32_t n, const int64_t *rp, const int32_t *col, int32_
     free(queue); free(mark);
     return added;
 }
+
+/* CSR of a dense bit-row graph: pass 1 (col == NULL) fills row_ptr and returns
+ * nnz; pass 2 fills col (ascending per row). */
+int64_t gg_dense_to_csr(int32_t n, int32_t words, const uint32_t *rows, int64_t *row_ptr, int32_t *col) {
+    if (!col) {
+        row_ptr[0] = 0;
+        for (int32_t v = 0; v < n; ++v) {
+            int64_t c = 0;
+            for (int32_t w = 0; w < words; ++w) c += __builtin_popcount(rows[(int64_t)v * words + w]);
+            row_ptr[v + 1] = row_ptr[v] + c;
+        }
+        return row_ptr[n];
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        int64_t k = row_ptr[v];
+        for (int32_t w = 0; w < words; ++w) {
+            uint32_t bits = rows[(int64_t)v * words + w];
+            while (bits) {
+                col[k++] = (w << 5) + __builtin_ctz(bits);
+                bits &= bits - 1;
+            }
+        }
+    }
+    return row_ptr[n];
+}

@@ -199,6 +199,59 @@ int cg_chordal_test_batch(cg_context *ctx, const cg_dense *graphs, int32_t count
 int cg_chordal_test_dense_noalloc(const cg_dense *g, cg_result *res, int32_t *order, cudaStream_t stream);
 
 /*
+ * Serving: a continuous-batching request queue (not part of the paper).
+ * Queries arrive one at a time (cg_queue_submit returns at once with a
+ * ticket); a worker thread owned by the queue admits pending queries in
+ * arrival order — graphs with n <= 4096 and larger graphs in two separate
+ * lanes, so short queries never wait behind long ones — into the next batch
+ * while the batch fits the queue's device memory budget and one of its
+ * `max_inflight` slots is free, launches each
+ * batch on its slot's stream (so queries that arrive while others run
+ * overlap with them on the GPU), and marks tickets done when the batch's
+ * event completes.  Dense queries and CSR queries with n <= 131072 and at
+ * least 16 neighbours per vertex on average (or n <= 4096) use the dense
+ * kernels (CSR rows are expanded to bits on the device); sparser CSR queries
+ * use the CSR kernels.  Results equal those of the single-graph entries.
+ * The graph memory of a query must stay valid until its ticket completes.
+ * While a queue runs, its context must not be used for autotuning.
+ */
+enum { CG_GRAPH_DENSE = 0, CG_GRAPH_CSR = 1 };
+typedef struct {
+    int32_t kind;     /* CG_GRAPH_DENSE or CG_GRAPH_CSR */
+    cg_dense dense;   /* used when kind == CG_GRAPH_DENSE (device rows) */
+    cg_csr csr;       /* used when kind == CG_GRAPH_CSR (device arrays) */
+} cg_graph_ref;
+
+typedef struct {
+    int64_t mem_budget_bytes; /* device pool for in-flight batches (0: 4 GiB), allocated at creation */
+    int32_t max_inflight;     /* concurrent batches / slot streams (0: 8) */
+    int32_t max_batch;        /* queries per batch of graphs with n <= 4096 (0: 1024) */
+    int32_t max_pending;      /* queued queries before submit returns CG_EAGAIN (0: 2^20) */
+    int32_t max_batch_large;  /* queries per batch of larger graphs (0: 4) */
+} cg_queue_config;
+
+typedef struct {
+    int64_t submitted, completed, pending, inflight, batches, pool_free_bytes;
+} cg_queue_info;
+
+typedef struct cg_queue cg_queue;
+
+int cg_queue_create(cg_context *ctx, const cg_queue_config *cfg, cg_queue **out);
+/* CG_EAGAIN when max_pending queries are waiting. */
+int cg_queue_submit(cg_queue *q, const cg_graph_ref *g, uint64_t *ticket);
+/* CG_OK and the result (HOST memory) once done — the ticket is then
+ * forgotten; CG_EAGAIN while pending; latency_s (nullable) gets
+ * submit-to-completion seconds (host steady clock).  A query that can never
+ * fit the memory budget completes with CG_ENOMEM. */
+int cg_queue_poll(cg_queue *q, uint64_t ticket, cg_result *host_res, double *latency_s);
+/* Waits until every submitted query completed; timeout_ns < 0 waits forever;
+ * CG_ETIMEOUT when the time runs out (no GPU wait is involved). */
+int cg_queue_drain(cg_queue *q, int64_t timeout_ns);
+int cg_queue_stats(cg_queue *q, cg_queue_info *out);
+/* Finishes queued work, stops the worker, frees the pool. */
+int cg_queue_destroy(cg_queue *q);
+
+/*
  * Per-phase timing (tracing aid; not part of the paper).  When enabled, each
  * call records CUDA events on the stream a phase runs on: around LexBFS
  * launches, around the check (check + finalize), around fused one-CTA

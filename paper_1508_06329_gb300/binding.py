@@ -48,6 +48,23 @@ class cg_profile(ctypes.Structure):
                 ("batch_calls", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
 
 
+class cg_graph_ref(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dense", cg_dense), ("csr", cg_csr)]
+
+
+class cg_queue_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_pending", ctypes.c_int32), ("max_batch_large", ctypes.c_int32)]
+
+
+class cg_queue_info(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "pending", "inflight", "batches",
+                                              "pool_free_bytes")]
+
+
+CG_GRAPH_DENSE, CG_GRAPH_CSR = 0, 1
+
+
 class cg_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("validate", ctypes.c_int32), ("threads_override", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
@@ -74,6 +91,12 @@ SIGNATURES = {
     "cg_chordal_test_csr_host": ([P, I32, I64, P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_dense_noalloc": ([P, P, P, P], ctypes.c_int),
     "cg_profile_enable": ([P, I32], ctypes.c_int),
+    "cg_queue_create": ([P, P, P], ctypes.c_int),
+    "cg_queue_submit": ([P, P, P], ctypes.c_int),
+    "cg_queue_poll": ([P, ctypes.c_uint64, P, P], ctypes.c_int),
+    "cg_queue_drain": ([P, I64], ctypes.c_int),
+    "cg_queue_stats": ([P, P], ctypes.c_int),
+    "cg_queue_destroy": ([P], ctypes.c_int),
     "cg_batch_plan_create": ([P, P, I32, P, P, P, P], ctypes.c_int),
     "cg_batch_plan_run": ([P, P], ctypes.c_int),
     "cg_batch_plan_destroy": ([P], ctypes.c_int),
@@ -133,6 +156,12 @@ cg_chordal_test_csr = _fn("cg_chordal_test_csr")
 cg_chordal_test_csr_host = _fn("cg_chordal_test_csr_host")
 cg_chordal_test_dense_noalloc = _fn("cg_chordal_test_dense_noalloc")
 cg_profile_enable = _fn("cg_profile_enable")
+cg_queue_create = _fn("cg_queue_create")
+cg_queue_submit = _fn("cg_queue_submit")
+cg_queue_poll = _fn("cg_queue_poll")
+cg_queue_drain = _fn("cg_queue_drain")
+cg_queue_stats = _fn("cg_queue_stats")
+cg_queue_destroy = _fn("cg_queue_destroy")
 cg_batch_plan_create = _fn("cg_batch_plan_create")
 cg_batch_plan_run = _fn("cg_batch_plan_run")
 cg_batch_plan_destroy = _fn("cg_batch_plan_destroy")
@@ -330,3 +359,59 @@ def autotune_get(ctx: Context) -> list:
 def autotune_set(ctx: Context, table) -> None:
     buf = (ctypes.c_int32 * 9)(*[int(x) for x in table][:9])
     _check(cg_autotune_set(ctx.handle, buf, 9))
+
+
+class Queue:
+    """Continuous-batching request queue (cg_queue_*).  Graph tensors passed to
+    submit_* must stay alive until their ticket completes (kept here)."""
+
+    def __init__(self, ctx: Context, mem_budget_bytes: int = 0, max_inflight: int = 0, max_batch: int = 0,
+                 max_pending: int = 0, max_batch_large: int = 0):
+        cfg = cg_queue_config(mem_budget_bytes, max_inflight, max_batch, max_pending, max_batch_large)
+        h = ctypes.c_void_p()
+        _check(cg_queue_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def _submit(self, ref, keep) -> int:
+        t = ctypes.c_uint64()
+        _check(cg_queue_submit(self.handle, ctypes.byref(ref), ctypes.byref(t)))
+        self._keep[t.value] = keep
+        return t.value
+
+    def submit_dense(self, rows, n: int) -> int:
+        ref = cg_graph_ref(CG_GRAPH_DENSE, dense_desc(rows, n), cg_csr())
+        return self._submit(ref, rows)
+
+    def submit_csr(self, row_ptr, col, n: int) -> int:
+        ref = cg_graph_ref(CG_GRAPH_CSR, cg_dense(), csr_desc(row_ptr, col, n))
+        return self._submit(ref, (row_ptr, col))
+
+    def poll(self, ticket: int):
+        """(status, (chordal, v, p, u), latency_s); status CG_EAGAIN while pending."""
+        r = cg_result()
+        lat = ctypes.c_double()
+        st = cg_queue_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(r), ctypes.byref(lat))
+        if st != CG_EAGAIN:
+            self._keep.pop(ticket, None)
+        return st, r.astuple(), lat.value
+
+    def drain(self, timeout_ns: int = -1) -> int:
+        return cg_queue_drain(self.handle, timeout_ns)
+
+    def stats(self) -> dict:
+        info = cg_queue_info()
+        _check(cg_queue_stats(self.handle, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in cg_queue_info._fields_}
+
+    def close(self):
+        if self.handle:
+            _check(cg_queue_destroy(self.handle))
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -7,7 +7,7 @@
 #include <new>
 #include <vector>
 
-#include "kernels.h"
+#include "host.h"
 
 namespace cg {
 
@@ -27,50 +27,7 @@ int set_error(int status, const char *fmt, ...) {
 
 using namespace cg;
 
-struct cg_context {
-    cg_config cfg{};
-    int num_sms = 0;
-    void *ws = nullptr;          // device workspace
-    size_t ws_bytes = 0;
-    void *pinned = nullptr;      // pinned host staging for descriptor uploads
-    size_t pinned_bytes = 0;
-    cudaEvent_t staged{};        // recorded after each staging upload
-    bool staged_pending = false;
-    // concurrent size buckets of a batch: forked streams and join events
-    static constexpr int kAux = 8;
-    static constexpr int kBuckets = 10;          // n in (2^(b+3), 2^(b+4)] for b < 9, then n > 4096
-    cudaStream_t aux[kAux]{};
-    cudaEvent_t fork{}, join[kBuckets]{};
-    int tuned_threads[kBuckets]{};               // 0 = size rule
-    // per-phase timing
-    bool profiling = false;
-    std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_lex, ev_check, ev_fused, ev_batch;
-    int64_t launches = 0;
-};
-
-namespace {
-
-constexpr size_t kAlign = 256;
-
-inline size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
-
-// Offsets into one workspace allocation.
-struct Carve {
-    size_t off = 0;
-    template <typename T>
-    size_t take(size_t count) {
-        off = align_up(off, kAlign);
-        const size_t o = off;
-        off += std::max<size_t>(count, 1) * sizeof(T);
-        return o;
-    }
-};
-
-template <typename T>
-T *at(cg_context *ctx, size_t off) {
-    return reinterpret_cast<T *>(static_cast<unsigned char *>(ctx->ws) + off);
-}
+namespace cg {
 
 int ensure_ws(cg_context *ctx, size_t bytes) {
     if (bytes <= ctx->ws_bytes) return CG_OK;
@@ -106,6 +63,23 @@ int ensure_pinned(cg_context *ctx, size_t bytes) {
     return CG_OK;
 }
 
+cudaError_t stream_set_create(StreamSet *ss) {
+    cudaError_t e = cudaEventCreateWithFlags(&ss->fork, cudaEventDisableTiming);
+    for (int i = 0; e == cudaSuccess && i < kBuckets; ++i) e = cudaEventCreateWithFlags(&ss->join[i], cudaEventDisableTiming);
+    for (int i = 0; e == cudaSuccess && i < StreamSet::kAux; ++i)
+        e = cudaStreamCreateWithFlags(&ss->aux[i], cudaStreamNonBlocking);
+    return e;
+}
+
+void stream_set_destroy(StreamSet *ss) {
+    if (ss->fork) cudaEventDestroy(ss->fork);
+    for (int i = 0; i < kBuckets; ++i)
+        if (ss->join[i]) cudaEventDestroy(ss->join[i]);
+    for (int i = 0; i < StreamSet::kAux; ++i)
+        if (ss->aux[i]) cudaStreamDestroy(ss->aux[i]);
+    *ss = StreamSet{};
+}
+
 cudaEvent_t take_event(cg_context *ctx) {
     if (!ctx->ev_free.empty()) {
         cudaEvent_t e = ctx->ev_free.back();
@@ -120,29 +94,22 @@ cudaEvent_t take_event(cg_context *ctx) {
     return e;
 }
 
-// Brackets one phase with events when profiling is on.
-struct PhaseTimer {
-    cg_context *ctx;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *list;
-    cudaStream_t stream;
-    cudaEvent_t a = nullptr;
-    PhaseTimer(cg_context *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *l, cudaStream_t s)
-        : ctx(c), list(l), stream(s) {
-        if (ctx->profiling && (a = take_event(ctx))) cudaEventRecord(a, stream);
+PhaseTimer::PhaseTimer(cg_context *c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *l, cudaStream_t s)
+    : ctx(c), list(l), stream(s) {
+    if (ctx && ctx->profiling && (a = take_event(ctx))) cudaEventRecord(a, stream);
+}
+
+void PhaseTimer::stop() {
+    if (!a) return;
+    cudaEvent_t b = take_event(ctx);
+    if (b) {
+        cudaEventRecord(b, stream);
+        list->emplace_back(a, b);
+    } else {
+        ctx->ev_free.push_back(a);
     }
-    void stop() {
-        if (!a) return;
-        cudaEvent_t b = take_event(ctx);
-        if (b) {
-            cudaEventRecord(b, stream);
-            list->emplace_back(a, b);
-        } else {
-            ctx->ev_free.push_back(a);
-        }
-        a = nullptr;
-    }
-    ~PhaseTimer() { stop(); }
-};
+    a = nullptr;
+}
 
 int check_ctx(cg_context *ctx) {
     if (!ctx) return set_error(CG_EINVAL, "null context");
@@ -168,7 +135,7 @@ int check_csr(const cg_csr *g) {
     return CG_OK;
 }
 
-DenseDesc desc_of(const cg_dense *g, int64_t vbase, int64_t obase, int32_t rindex = 0) {
+DenseDesc desc_of(const cg_dense *g, int64_t vbase, int64_t obase, int32_t rindex) {
     DenseDesc d{};
     d.rows = g->rows;
     d.n = g->n;
@@ -191,21 +158,6 @@ int bucket_of(int n) {
     while (b < 8 && n > (16 << b)) ++b;
     return b;
 }
-
-struct BatchLayout {
-    struct Bucket {
-        int begin = 0, end = 0, nmax = 0;
-        FusedPlan fplan{};
-        LexPlan lplan{};
-        int ctas = 0;
-        int64_t vbegin = 0, vend = 0;   // packed vertex range (bucket 9)
-    };
-    int count = 0;
-    std::vector<DenseDesc> descs;      // bucket order
-    std::vector<int64_t> voff;         // packed vertex offset of each desc (+ total)
-    Bucket bk[cg_context::kBuckets];
-    int64_t total = 0;
-};
 
 int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const int64_t *order_offsets,
                 BatchLayout *L) {
@@ -232,7 +184,7 @@ int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const in
         obase[k] = order_offsets ? order_offsets[k] : packed;
         packed += graphs[k].n;
     }
-    for (int b = 0; b < cg_context::kBuckets; ++b) L->bk[b] = BatchLayout::Bucket{};
+    for (int b = 0; b < kBuckets; ++b) L->bk[b] = BatchLayout::Bucket{};
     for (int j = 0; j < count; ++j) {
         const int k = idx[j];
         L->voff[j] = total;
@@ -242,7 +194,7 @@ int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const in
     L->voff[count] = total;
     L->total = total;
     int j = 0;
-    for (int b = 0; b < cg_context::kBuckets; ++b) {
+    for (int b = 0; b < kBuckets; ++b) {
         auto &B = L->bk[b];
         B.begin = j;
         while (j < count && bucket[idx[j]] == b) ++j;
@@ -266,11 +218,6 @@ int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const in
     return CG_OK;
 }
 
-// Device buffers a batch needs (offsets into one allocation).
-struct BatchBuffers {
-    size_t o_desc, o_voff, o_order, o_pos, o_parent, o_keys, o_counter, o_gstate, bytes;
-};
-
 BatchBuffers batch_buffers(const BatchLayout &L, bool need_order) {
     Carve cv;
     BatchBuffers bb{};
@@ -280,7 +227,7 @@ BatchBuffers batch_buffers(const BatchLayout &L, bool need_order) {
     bb.o_pos = cv.take<int32_t>(L.total);
     bb.o_parent = cv.take<int32_t>(L.total);
     bb.o_keys = cv.take<unsigned long long>(L.count);
-    bb.o_counter = cv.take<int>(cg_context::kBuckets * 64);
+    bb.o_counter = cv.take<int>(kBuckets * 64);
     const auto &B9 = L.bk[9];
     bb.o_gstate = cv.take<unsigned char>(B9.end > B9.begin && B9.lplan.wide_ids ? B9.lplan.gstate_bytes * B9.ctas : 0);
     bb.bytes = cv.off;
@@ -291,8 +238,9 @@ BatchBuffers batch_buffers(const BatchLayout &L, bool need_order) {
 // into `stream`.  base: device allocation laid out by batch_buffers (the
 // descriptors and offsets must already be there).
 int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb, unsigned char *base,
-                  int32_t *orders, cg_result *res, cudaStream_t stream) {
+                  int32_t *orders, cg_result *res, cudaStream_t stream, const StreamSet &ss, bool account) {
     int rc;
+    cg_context *tctx = account ? ctx : nullptr;   // timers and launch counts only for the caller's thread
     auto P = [&](size_t off) { return base + off; };
     const DenseDesc *ddesc = reinterpret_cast<const DenseDesc *>(P(bb.o_desc));
     const int64_t *dvoff = reinterpret_cast<const int64_t *>(P(bb.o_voff));
@@ -301,54 +249,63 @@ int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
     int32_t *parent = reinterpret_cast<int32_t *>(P(bb.o_parent));
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(P(bb.o_keys));
     int *counters = reinterpret_cast<int *>(P(bb.o_counter));
-    CG_CUDA_TRY(cudaEventRecord(ctx->fork, stream));
+    CG_CUDA_TRY(cudaEventRecord(ss.fork, stream));
     int used = 0;
-    for (int b = 0; b < cg_context::kBuckets; ++b) {
+    for (int b = 0; b < kBuckets; ++b) {
         const auto &B = L.bk[b];
         const int cnt = B.end - B.begin;
         if (cnt <= 0) continue;
-        cudaStream_t s = ctx->aux[used % cg_context::kAux];
-        CG_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fork, 0));
+        cudaStream_t s = ss.aux[used % StreamSet::kAux];
+        CG_CUDA_TRY(cudaStreamWaitEvent(s, ss.fork, 0));
         if (b < 9) {
-            PhaseTimer pt(ctx, &ctx->ev_fused, s);
+            PhaseTimer pt(tctx, &ctx->ev_fused, s);
             if ((rc = fused_dense_launch(B.fplan, ddesc + B.begin, cnt, B.ctas, order, pos, parent, res,
                                          counters + 64 * b, s)))
                 return rc;
-            ctx->launches += 1;
+            if (account) ctx->launches += 1;
         } else {
             {
-                PhaseTimer pt(ctx, &ctx->ev_lex, s);
+                PhaseTimer pt(tctx, &ctx->ev_lex, s);
                 if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, parent,
                                               B.lplan.wide_ids ? P(bb.o_gstate) : nullptr, counters + 64 * b, s)))
                     return rc;
             }
-            PhaseTimer pt(ctx, &ctx->ev_check, s);
+            PhaseTimer pt(tctx, &ctx->ev_check, s);
             // the check over this bucket's vertices (a slice of the offset table)
             if ((rc = peo_dense_launch(ddesc + B.begin, DenseDesc{}, cnt, dvoff + B.begin, B.vend - B.vbegin, order,
                                        pos, parent, true, keys + B.begin, ctx->num_sms, s)))
                 return rc;
             if ((rc = finalize_launch(ddesc + B.begin, DenseDesc{}, cnt, keys + B.begin, order, parent, res, s)))
                 return rc;
-            ctx->launches += 3;
+            if (account) ctx->launches += 3;
         }
-        CG_CUDA_TRY(cudaEventRecord(ctx->join[b], s));
-        CG_CUDA_TRY(cudaStreamWaitEvent(stream, ctx->join[b], 0));
+        CG_CUDA_TRY(cudaEventRecord(ss.join[b], s));
+        CG_CUDA_TRY(cudaStreamWaitEvent(stream, ss.join[b], 0));
         ++used;
     }
+    return CG_OK;
+}
+
+size_t layout_staging_bytes(const BatchLayout &L) {
+    return align_up(sizeof(DenseDesc) * L.count, 16) + sizeof(int64_t) * (L.count + 1) + 64;
+}
+
+int upload_layout_to(const BatchLayout &L, const BatchBuffers &bb, unsigned char *base, unsigned char *staging,
+                     cudaStream_t stream) {
+    const size_t bytes_desc = sizeof(DenseDesc) * L.count, bytes_voff = sizeof(int64_t) * (L.count + 1);
+    std::memcpy(staging, L.descs.data(), bytes_desc);
+    std::memcpy(staging + align_up(bytes_desc, 16), L.voff.data(), bytes_voff);
+    CG_CUDA_TRY(cudaMemcpyAsync(base + bb.o_desc, staging, bytes_desc, cudaMemcpyHostToDevice, stream));
+    CG_CUDA_TRY(cudaMemcpyAsync(base + bb.o_voff, staging + align_up(bytes_desc, 16), bytes_voff,
+                                cudaMemcpyHostToDevice, stream));
     return CG_OK;
 }
 
 int upload_layout(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb, unsigned char *base,
                   cudaStream_t stream) {
     int rc;
-    const size_t bytes_desc = sizeof(DenseDesc) * L.count, bytes_voff = sizeof(int64_t) * (L.count + 1);
-    if ((rc = ensure_pinned(ctx, align_up(bytes_desc, 16) + bytes_voff + 64))) return rc;
-    unsigned char *hp = static_cast<unsigned char *>(ctx->pinned);
-    std::memcpy(hp, L.descs.data(), bytes_desc);
-    std::memcpy(hp + align_up(bytes_desc, 16), L.voff.data(), bytes_voff);
-    CG_CUDA_TRY(cudaMemcpyAsync(base + bb.o_desc, hp, bytes_desc, cudaMemcpyHostToDevice, stream));
-    CG_CUDA_TRY(cudaMemcpyAsync(base + bb.o_voff, hp + align_up(bytes_desc, 16), bytes_voff, cudaMemcpyHostToDevice,
-                                stream));
+    if ((rc = ensure_pinned(ctx, layout_staging_bytes(L)))) return rc;
+    if ((rc = upload_layout_to(L, bb, base, static_cast<unsigned char *>(ctx->pinned), stream))) return rc;
     CG_CUDA_TRY(cudaEventRecord(ctx->staged, stream));
     ctx->staged_pending = true;
     return CG_OK;
@@ -436,7 +393,7 @@ int run_single_csr(cg_context *ctx, const cg_csr *g, int32_t *order_out, int32_t
     return finalize_launch(nullptr, d, 1, key, order, parent, res, stream);
 }
 
-}  // namespace
+}  // namespace cg
 
 extern "C" {
 
@@ -458,11 +415,7 @@ int cg_context_create(const cg_config *cfg, cg_context **out) {
     cudaError_t e = cudaSetDevice(ctx->cfg.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->cfg.device);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
-    for (int i = 0; e == cudaSuccess && i < cg_context::kBuckets; ++i)
-        e = cudaEventCreateWithFlags(&ctx->join[i], cudaEventDisableTiming);
-    for (int i = 0; e == cudaSuccess && i < cg_context::kAux; ++i)
-        e = cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = stream_set_create(&ctx->streams);
     if (e != cudaSuccess) {
         delete ctx;
         return set_error(CG_ECUDA, "context creation on device %d failed: %s", cfg ? cfg->device : 0,
@@ -519,9 +472,7 @@ int cg_context_destroy(cg_context *ctx) {
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     cudaEventDestroy(ctx->staged);
-    cudaEventDestroy(ctx->fork);
-    for (int i = 0; i < cg_context::kBuckets; ++i) cudaEventDestroy(ctx->join[i]);
-    for (int i = 0; i < cg_context::kAux; ++i) cudaStreamDestroy(ctx->aux[i]);
+    stream_set_destroy(&ctx->streams);
     delete ctx;
     return CG_OK;
 }
@@ -689,7 +640,7 @@ int cg_chordal_test_batch(cg_context *ctx, const cg_dense *graphs, int32_t count
     unsigned char *base = static_cast<unsigned char *>(ctx->ws);
     if ((rc = upload_layout(ctx, L, bb, base, stream))) return rc;
     PhaseTimer pt(ctx, &ctx->ev_batch, stream);
-    return enqueue_batch(ctx, L, bb, base, orders, res, stream);
+    return enqueue_batch(ctx, L, bb, base, orders, res, stream, ctx->streams, true);
 }
 
 struct cg_batch_plan {
@@ -719,7 +670,7 @@ int cg_batch_plan_create(cg_context *ctx, const cg_dense *graphs, int32_t count,
         return set_error(CG_ENOMEM, "plan buffers (%zu bytes) allocation failed", bb.bytes);
     }
     unsigned char *base = static_cast<unsigned char *>(plan->mem);
-    cudaStream_t cs = ctx->aux[cg_context::kAux - 1];
+    cudaStream_t cs = ctx->streams.aux[StreamSet::kAux - 1];
     rc = upload_layout(ctx, L, bb, base, cs);
     if (rc == CG_OK) {
         cudaError_t e = cudaStreamSynchronize(cs);
@@ -736,7 +687,7 @@ int cg_batch_plan_create(cg_context *ctx, const cg_dense *graphs, int32_t count,
         cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) rc = set_error(CG_ECUDA, "begin capture failed: %s", cudaGetErrorString(e));
         if (rc == CG_OK) {
-            const int erc = enqueue_batch(ctx, L, bb, base, orders, res, origin);
+            const int erc = enqueue_batch(ctx, L, bb, base, orders, res, origin, ctx->streams, true);
             e = cudaStreamEndCapture(origin, &plan->graph);
             if (erc) rc = erc;
             else if (e != cudaSuccess) rc = set_error(CG_ECUDA, "end capture failed: %s", cudaGetErrorString(e));
@@ -842,13 +793,13 @@ int cg_batch_autotune(cg_context *ctx, const cg_dense *graphs, int32_t count, cu
 
 int cg_autotune_get(cg_context *ctx, int32_t *threads, int32_t slots) {
     if (!ctx || !threads) return set_error(CG_EINVAL, "null argument");
-    for (int i = 0; i < slots && i < cg_context::kBuckets; ++i) threads[i] = ctx->tuned_threads[i];
+    for (int i = 0; i < slots && i < kBuckets; ++i) threads[i] = ctx->tuned_threads[i];
     return CG_OK;
 }
 
 int cg_autotune_set(cg_context *ctx, const int32_t *threads, int32_t slots) {
     if (!ctx || !threads) return set_error(CG_EINVAL, "null argument");
-    for (int i = 0; i < slots && i < cg_context::kBuckets; ++i) {
+    for (int i = 0; i < slots && i < kBuckets; ++i) {
         const int t = threads[i];
         if (i < 9 && t != 0 && t != 64 && t != 128 && t != 256 && t != 512)
             return set_error(CG_EINVAL, "bucket %d: CTA size %d not in {0, 64, 128, 256, 512}", i, t);
