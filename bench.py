@@ -11,6 +11,9 @@ Other workloads (same JSON line; not run by default):
   sparse1m   the N=2^20 CSR pair (reversed-PEO chordal / cycle-closing edges),
              the two graphs on two streams
   batch4096  4,096 graphs, N log-uniform in [16, 2048], one captured batch plan
+  paper7     the paper's Section 7 families on GB300 beside the CPU oracle:
+             cliques N = 1000..11000, dense random (p = 0.5), sparse random
+             (M = 20N), trees and chordal graphs at N = 10,000; one table
   serve      Poisson stream of 100,000 queries (continuous-batching queue) drawn
              from a seeded pool of 64 graphs: N log-uniform in [64, 65536],
              density U[0.01, 0.2], dense below N = 8,192, CSR above; arrival
@@ -104,6 +107,19 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def aggregate_over_ranks(local_ms: float, tests_per_rank: int, device=None):
+    """Whole-job timing of replicas: the slowest rank's timed total and the
+    rate of all ranks' tests over it (a no-op without torch.distributed)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    return total_ms, tests_per_rank * world / (total_ms / 1e3)
 
 
 def dist_info():
@@ -339,6 +355,83 @@ def run_serve(args):
     return 0 if bad == 0 else 1
 
 
+def paper7_graphs():
+    """Seeded stand-ins for the paper's test classes (Section 7): it gives no
+    generator parameters, so dense random uses p = 0.5 and the chordal class
+    spans tree sizes 50..10000 (dense to sparse)."""
+    import graphgen as gg
+    out = []
+    for n in range(1000, 12000, 1000):
+        out.append(("clique", f"N={n}", gg.clique(n)))
+    for t in range(5):
+        out.append(("dense random", f"test{t + 1}", gg.random_dense(10000, 0.5, gg.SEED_BASE + 70 + t)))
+    for t in range(5):
+        out.append(("sparse random M=20N", f"test{t + 1}", gg.random_dense(10000, 40.0 / 9999, gg.SEED_BASE + 80 + t)))
+    for t in range(7):
+        out.append(("tree", f"test{t + 1}", gg.random_tree(10000, gg.SEED_BASE + 90 + t)))
+    for t, tn in enumerate((50, 100, 200, 500, 1000, 2000, 5000, 10000)):
+        out.append(("chordal (subtree model)", f"test{t + 1} tree={tn}", gg.subtree_dense(10000, tn, gg.SEED_BASE + 100 + t)))
+    return out
+
+
+def run_paper7(args):
+    """GPU vs oracle on the paper's families, one graph at a time (rank 0)."""
+    import numpy as np
+    import torch
+    import oracle
+    rank, world, local = dist_info()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1508_06329_gb300 import build as cbuild
+    cbuild.build()
+    from paper_1508_06329_gb300 import binding as B
+    ctx = B.Context(local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    table, gpu_total_ms, tests = [], 0.0, 0
+    for fam, label, g in paper7_graphs():
+        rows = torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).to(dev)
+        res = torch.empty(4, dtype=torch.int32, device=dev)
+        B.chordal_test_dense(ctx, rows, g.n, res)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(3):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            B.chordal_test_dense(ctx, rows, g.n, res)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        hr = torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).pin_memory()
+        t0 = time.perf_counter()
+        got = B.chordal_test_dense_host(ctx, hr, g.n)
+        e2e_ms = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        want = oracle.chordal_test(g)
+        oracle_ms = (time.perf_counter() - t0) * 1e3
+        if got != want.witness or tuple(res.cpu().tolist()) != want.witness:
+            raise SystemExit(f"parity failure on {fam} {label}")
+        gpu_ms = statistics.median(ms)
+        gpu_total_ms += gpu_ms
+        tests += 1
+        table.append({"family": fam, "case": label, "n": g.n, "m": g.num_edges(), "chordal": want.chordal,
+                      "gpu_ms": round(gpu_ms, 3), "gpu_e2e_ms": round(e2e_ms, 3), "oracle_ms": round(oracle_ms, 3),
+                      "oracle_over_gpu": round(oracle_ms / gpu_ms, 2)})
+    line = {"metric": METRIC, "value": tests / (gpu_total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 3,
+            "warmup": 1, "ms_per_step": gpu_total_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 bitsets / int32 (exact)", "data": "synthetic",
+            "config": {"workload": "paper Section 7 families, one graph at a time (median of 3, L2 flushed)",
+                       "gpu_ms": "LexBFS + check kernels, CUDA events",
+                       "gpu_e2e_ms": "host rows -> device -> result (cg_chordal_test_dense_host)",
+                       "oracle_ms": "single-threaded C oracle, input already in memory"},
+            "table": table}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -428,13 +521,7 @@ def run_gpu(args):
             prof[k] = prof.get(k, 0) + v
         c.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    tests = ngraph * args.steps * world
-    value = tests / (total_ms / 1e3)
+    total_ms, value = aggregate_over_ranks(sum(step_ms), ngraph * args.steps, dev)
 
     # ---- end to end through the public API with host buffers
     e2e_steps = max(1, min(args.steps, 5 if wl != "sparse1m" else 1))
@@ -569,12 +656,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dense16k",
-                    choices=["dense16k", "small1k", "sparse1m", "batch4096", "serve"])
+                    choices=["dense16k", "small1k", "sparse1m", "batch4096", "serve", "paper7"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "paper7":
+        return run_paper7(args)
     return run_gpu(args)
 
 

@@ -134,8 +134,9 @@ __device__ __forceinline__ void prefetch_range_l2(const void *base, size_t bytes
 // One CTA computes the LexBFS order of one graph.  rows/stride address the
 // adjacency (global memory, or a compact shared-memory copy).  parent may be
 // null; otherwise parent[v] receives p(v) (or -1 when v has no earlier
-// neighbour).  LPW threads share each row word (thread t takes bit slice
-// t % LPW of word t / LPW + k * T / LPW), which shortens the serial bit loop.
+// neighbour).  lpw >= LPW threads share each row word (thread t takes bit
+// slice t % lpw of word t / lpw + k * T / lpw), which shortens the serial bit
+// loop; lpw grows while T / lpw still covers the row.
 template <typename Id, int T, int WPT, int LPW>
 __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n, LexState<Id> st,
                            LexScalars *sc, int32_t *__restrict__ order, int32_t *__restrict__ pos,
@@ -146,13 +147,17 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
     const Id kNone = (Id)(kNumbered - 1);
     const int t = threadIdx.x;
     if (n <= 0) return;
-    constexpr int kGroups = T / LPW;            // word slots per k
-    constexpr int kSlice = 32 / LPW;            // bits per thread
-    const int wt = t / LPW;
-    const uint32_t part = LPW == 1 ? 0xFFFFFFFFu
-                                   : (((1u << kSlice) - 1u) << ((t % LPW) * kSlice));
-    const Id HEAD = (Id)n;
     const int wn = (n + 31) >> 5;
+    // lanes per word: at least LPW, more while the row still has a word slot
+    // per thread group, so short rows spread their bits over all threads
+    int lpw = LPW;
+    while (lpw < 32 && T / (lpw * 2) >= wn) lpw *= 2;
+    const int kGroups = T / lpw;                // word slots per k
+    const int kSlice = 32 / lpw;                // bits per thread
+    const int wt = t / lpw;
+    const uint32_t part = lpw == 1 ? 0xFFFFFFFFu
+                                   : ((kSlice == 32 ? 0xFFFFFFFFu : ((1u << kSlice) - 1u)) << ((t % lpw) * kSlice));
+    const Id HEAD = (Id)n;
     const uint32_t lastmask = (n & 31) ? ((1u << (n & 31)) - 1u) : 0xFFFFFFFFu;
 
     for (int v = t; v < n; v += T) {
