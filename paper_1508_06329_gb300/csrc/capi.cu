@@ -229,7 +229,7 @@ BatchBuffers batch_buffers(const BatchLayout &L, bool need_order) {
     bb.o_keys = cv.take<unsigned long long>(L.count);
     bb.o_counter = cv.take<int>(kBuckets * 64);
     const auto &B9 = L.bk[9];
-    bb.o_gstate = cv.take<unsigned char>(B9.end > B9.begin && B9.lplan.wide_ids ? B9.lplan.gstate_bytes * B9.ctas : 0);
+    bb.o_gstate = cv.take<unsigned char>(B9.end > B9.begin ? B9.lplan.gstate_bytes * B9.ctas : 0);
     bb.bytes = cv.off;
     return bb;
 }
@@ -267,7 +267,7 @@ int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
             {
                 PhaseTimer pt(tctx, &ctx->ev_lex, s);
                 if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, parent,
-                                              B.lplan.wide_ids ? P(bb.o_gstate) : nullptr, counters + 64 * b, s)))
+                                              B.lplan.gstate_bytes ? P(bb.o_gstate) : nullptr, counters + 64 * b, s)))
                     return rc;
             }
             PhaseTimer pt(tctx, &ctx->ev_check, s);
@@ -324,7 +324,7 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
     const size_t o_parent = cv.take<int32_t>(n);
     const size_t o_key = cv.take<unsigned long long>(1);
     const size_t o_counter = cv.take<int>(1);
-    const size_t o_gstate = cv.take<unsigned char>(plan.wide_ids ? plan.gstate_bytes : 0);
+    const size_t o_gstate = cv.take<unsigned char>(plan.gstate_bytes);
     if ((rc = ensure_ws(ctx, cv.off))) return rc;
     int32_t *order = order_out ? order_out : at<int32_t>(ctx, o_order);
     int32_t *pos = pos_out ? pos_out : at<int32_t>(ctx, o_pos);
@@ -333,7 +333,7 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
     if (n > 0) {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
         rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, res ? parent : nullptr,
-                                 plan.wide_ids ? at<void>(ctx, o_gstate) : nullptr, at<int>(ctx, o_counter), stream);
+                                 plan.gstate_bytes ? at<void>(ctx, o_gstate) : nullptr, at<int>(ctx, o_counter), stream);
         if (rc) return rc;
         ctx->launches += 1;
     }
@@ -531,7 +531,7 @@ int cg_chordal_test_dense_host(cg_context *ctx, int32_t n, int32_t words_per_row
     cv.take<int32_t>(n);
     cv.take<unsigned long long>(1);
     cv.take<int>(1);
-    cv.take<unsigned char>(plan.wide_ids ? plan.gstate_bytes : 0);
+    cv.take<unsigned char>(plan.gstate_bytes);
     const size_t bytes_rows = (size_t)n * words_per_row * sizeof(uint32_t);
     const size_t o_rows = cv.take<unsigned char>(bytes_rows);
     const size_t o_res = cv.take<cg_result>(1);

@@ -3,7 +3,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/chordal.h"
+#include "chordal.h"
 
 namespace cg {
 

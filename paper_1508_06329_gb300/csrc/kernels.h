@@ -13,8 +13,9 @@ struct LexPlan {
     int threads;        // CTA size
     bool rows_smem;     // adjacency copied into shared memory
     bool wide_ids;      // 32-bit ids, state in a global workspace
+    bool split_state;   // 16-bit ids, class ids in shared memory, class arrays in a global workspace
     size_t smem_bytes;  // dynamic shared memory per CTA
-    size_t gstate_bytes;// global state bytes per CTA (wide ids only)
+    size_t gstate_bytes;// global state bytes per CTA (0: none)
 };
 
 // Picks the kernel variant for graphs of at most n_max vertices.

@@ -9,10 +9,11 @@ namespace cg {
 namespace {
 
 constexpr size_t kSmemLimit = 227 * 1024;   // opt-in dynamic shared memory per CTA (sm_100 family)
-constexpr int kSmemMaxN = 16384;             // 16-bit ids
+constexpr int kSmemMaxN = 16384;             // 16-bit ids, whole state in shared memory
+constexpr int kSplitMaxN = 65520;            // 16-bit ids, class ids in shared memory, class arrays global
 constexpr int kWideMaxN = 131072;            // 32-bit ids: 4 words per thread at 1024 threads
 
-template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM>
+template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, bool SPLIT = false>
 __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
                                                          int count, int32_t *__restrict__ order,
                                                          int32_t *__restrict__ pos, int32_t *__restrict__ parent,
@@ -31,7 +32,10 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
         const int n = d.n;
         LexState<Id> st;
         unsigned char *p = free_smem;
-        if (gstate) {
+        if (SPLIT) {
+            st = lex_state_carve_split<Id>(p, gstate + (size_t)blockIdx.x * gstate_stride, n);
+            p += lex_split_smem_bytes<Id>(n);
+        } else if (gstate) {
             st = lex_state_carve<Id>(gstate + (size_t)blockIdx.x * gstate_stride, n);
         } else {
             st = lex_state_carve<Id>(p, n);
@@ -59,11 +63,11 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
     }
 }
 
-template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM>
+template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, bool SPLIT = false>
 int launch_variant(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                    int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
                    cudaStream_t stream) {
-    auto kern = lexbfs_dense_kernel<Id, T, WPT, LPW, ROWS_SMEM>;
+    auto kern = lexbfs_dense_kernel<Id, T, WPT, LPW, ROWS_SMEM, SPLIT>;
     CG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes));
     if (count > 1) CG_CUDA_TRY(cudaMemsetAsync(work_counter, 0, sizeof(int), stream));
     kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, single, count, order, pos, parent,
@@ -94,6 +98,13 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
         p.threads = std::min(th, 1024);
         p.smem_bytes = kLexScalarBytes + state + (p.rows_smem ? rows : 0);
         p.gstate_bytes = 0;
+    } else if (n <= kSplitMaxN) {
+        p.wide_ids = false;
+        p.split_state = true;
+        p.rows_smem = false;
+        p.threads = 1024;
+        p.smem_bytes = kLexScalarBytes + lex_split_smem_bytes<uint16_t>(n);
+        p.gstate_bytes = lex_split_global_bytes<uint16_t>(n);
     } else {
         p.wide_ids = true;
         p.rows_smem = false;
@@ -112,6 +123,9 @@ int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc s
                         cudaStream_t stream) {
     if (count <= 0) return CG_OK;
     ctas = std::max(1, std::min(ctas, count));
+    if (plan.split_state)
+        return launch_variant<uint16_t, 1024, 2, 1, false, true>(plan, descs, single, count, ctas, order, pos, parent,
+                                                                  gstate, work_counter, stream);
     if (plan.wide_ids)
         return launch_variant<uint32_t, 1024, 4, 1, false>(plan, descs, single, count, ctas, order, pos, parent, gstate,
                                                          work_counter, stream);

@@ -28,8 +28,9 @@
 //     A known pivot's row is requested right after the first barrier, so its
 //     load overlaps the list update.  Two __syncthreads per step;
 //   * a shared bitmask of numbered vertices filters each pivot row, so only
-//     unnumbered neighbours are visited, and the deferred relabel and the
-//     split share one loop over a word's bits;
+//     unnumbered neighbours are visited; the deferred relabel and the split
+//     are two short loops over a word's bits, and a thread posts only its
+//     first (lowest) candidate of the top class to the pivot atomicMin;
 //   * every moved vertex y records parent[y] = x; the last pivot that moves y
 //     is its neighbour with the largest order index below its own, i.e.
 //     p(y) of the perfect-elimination check (Section 5.3), so the check does
@@ -102,6 +103,39 @@ __device__ inline LexState<Id> lex_state_carve(unsigned char *base, int n) {
 }
 
 constexpr size_t kLexScalarBytes = (sizeof(LexScalars) + 15) & ~size_t(15);
+
+// Split layout for graphs too large for the whole state in shared memory but
+// within 16-bit ids: the per-vertex class ids and the numbered bitmask (read
+// and written for every moved vertex and by class scans) stay in shared
+// memory; the per-class arrays go to a global workspace.
+template <typename Id>
+__host__ __device__ inline size_t lex_split_smem_bytes(int n) {
+    size_t b = ((size_t)n * sizeof(Id) + 15) & ~size_t(15);
+    b += (size_t)((n + 31) / 32) * sizeof(uint32_t);
+    return (b + 15) & ~size_t(15);
+}
+
+template <typename Id>
+__host__ __device__ inline size_t lex_split_global_bytes(int n) {
+    using Sz = typename IdTraits<Id>::Sz;
+    const size_t b = (size_t)n * sizeof(Sz) + (size_t)n * sizeof(Id) * 2 + (size_t)(n + 1) * sizeof(Id) * 2;
+    return (b + 255) & ~size_t(255);
+}
+
+template <typename Id>
+__device__ inline LexState<Id> lex_state_carve_split(unsigned char *smem, unsigned char *gmem, int n) {
+    using Sz = typename IdTraits<Id>::Sz;
+    LexState<Id> s;
+    s.cls = reinterpret_cast<Id *>(smem);
+    s.numbered = reinterpret_cast<uint32_t *>(smem + (((size_t)n * sizeof(Id) + 15) & ~size_t(15)));
+    s.sz = reinterpret_cast<Sz *>(gmem);
+    Id *p = reinterpret_cast<Id *>(gmem + (size_t)n * sizeof(Sz));
+    s.child = p;
+    s.freel = p + n;
+    s.cnext = p + 2 * (size_t)n;
+    s.cprev = p + 3 * (size_t)n + 1;
+    return s;
+}
 
 // Word w of row x, padding bits cleared.
 __device__ __forceinline__ uint32_t row_word(const uint32_t *__restrict__ rows, int stride, int x, int w,
@@ -212,26 +246,33 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                 const uint32_t prev = row_prev[k];
                 uint32_t nb = st.numbered[w];
                 const uint32_t cur = row_cur[k] & ~nb;  // unnumbered neighbours of x
-                uint32_t bits = prev | cur;
+                // relabel pass: vertices moved by the previous pivot take their new class
+                uint32_t bits = prev;
+                while (bits) {
+                    const int y = (w << 5) + (__ffs(bits) - 1);
+                    bits &= bits - 1;
+                    st.cls[y] = st.child[st.cls[y]];
+                }
+                // split pass: count moved members per class; a lane's first moved
+                // member of the top class (or of the next one) is its pivot candidate
+                bits = cur;
+                bool f_done = false, g_done = false;
                 while (bits) {
                     const int b = __ffs(bits) - 1;
                     const uint32_t bit = 1u << b;
                     bits &= bits - 1;
                     const int y = (w << 5) + b;
-                    Id c = st.cls[y];
-                    if (prev & bit) {  // moved by the previous pivot: finish its relabel
-                        c = st.child[c];
-                        st.cls[y] = c;
+                    const Id c = st.cls[y];
+                    const Sz old = atomicAdd(&st.sz[c], (Sz)1 << Tr::kShift);
+                    if ((old >> Tr::kShift) == 0) am |= bit;
+                    if (!f_done && c == f) {
+                        atomicMin(&sc->front_min[slot], (unsigned)y);
+                        f_done = true;
+                    } else if (!g_done && c == g) {
+                        atomicMin(&sc->second_min[slot], (unsigned)y);
+                        g_done = true;
                     }
-                    if (cur & bit) {
-                        const Sz old = atomicAdd(&st.sz[c], (Sz)1 << Tr::kShift);
-                        if ((old >> Tr::kShift) == 0) am |= bit;
-                        if (c == f)
-                            atomicMin(&sc->front_min[slot], (unsigned)y);
-                        else if (c == g)
-                            atomicMin(&sc->second_min[slot], (unsigned)y);
-                        if (parent) parent[y] = x;
-                    }
+                    if (parent) parent[y] = x;
                 }
                 if (w == (x >> 5) && ((part >> (x & 31)) & 1u)) {
                     st.cls[x] = kNumbered;

@@ -99,7 +99,7 @@ extern "C" int cg_chordal_test_dense_noalloc(const cg_dense *g, cg_result *res, 
     const int n = g->n;
     LexPlan plan;
     if ((rc = lexbfs_dense_plan(n, 0, &plan))) return rc;
-    if (plan.wide_ids) return set_error(CG_EINVAL, "no-allocation path needs the shared-memory variant");
+    if (plan.gstate_bytes) return set_error(CG_EINVAL, "no-allocation path needs the shared-memory variant");
     int32_t *pos = reinterpret_cast<int32_t *>(scratch + kOffPos);
     int32_t *parent = reinterpret_cast<int32_t *>(scratch + kOffParent);
     int32_t *ord = order ? order : reinterpret_cast<int32_t *>(scratch + kOffOrder);

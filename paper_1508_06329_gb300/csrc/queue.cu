@@ -125,7 +125,7 @@ struct Slot {
 // batch size is computed before a batch is admitted.
 size_t dense_need(int n) {
     return align_up(3 * (size_t)n * 4 + 64 + 16, kAlign) * 2 +
-           (n > 16384 ? align_up(lex_state_bytes<uint32_t>(n), kAlign) : 0);
+           (n > 16384 ? align_up(lex_state_bytes<uint32_t>(n), kAlign) : 0);   // covers the split layout too
 }
 
 }  // namespace
