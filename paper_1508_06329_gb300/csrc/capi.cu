@@ -266,14 +266,14 @@ int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
         } else {
             {
                 PhaseTimer pt(tctx, &ctx->ev_lex, s);
-                if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, parent,
+                if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, nullptr,
                                               B.lplan.gstate_bytes ? P(bb.o_gstate) : nullptr, counters + 64 * b, s)))
                     return rc;
             }
             PhaseTimer pt(tctx, &ctx->ev_check, s);
             // the check over this bucket's vertices (a slice of the offset table)
             if ((rc = peo_dense_launch(ddesc + B.begin, DenseDesc{}, cnt, dvoff + B.begin, B.vend - B.vbegin, order,
-                                       pos, parent, true, keys + B.begin, ctx->num_sms, s)))
+                                       pos, parent, false, keys + B.begin, ctx->num_sms, s)))
                 return rc;
             if ((rc = finalize_launch(ddesc + B.begin, DenseDesc{}, cnt, keys + B.begin, order, parent, res, s)))
                 return rc;
@@ -332,7 +332,9 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
     const DenseDesc d = desc_of(g, 0, 0);
     if (n > 0) {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
-        rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, res ? parent : nullptr,
+        // parents are recomputed by the check: per-step parent stores in the
+        // search cost more than the check's rescan (measured on N = 16,384)
+        rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, nullptr,
                                  plan.gstate_bytes ? at<void>(ctx, o_gstate) : nullptr, at<int>(ctx, o_counter), stream);
         if (rc) return rc;
         ctx->launches += 1;
@@ -340,7 +342,7 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
     if (!res) return CG_OK;
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
     unsigned long long *key = at<unsigned long long>(ctx, o_key);
-    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, true, key, ctx->num_sms, stream)))
+    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream)))
         return rc;
     ctx->launches += n > 0 ? 2 : 1;
     return finalize_launch(nullptr, d, 1, key, order, parent, res, stream);
