@@ -10,6 +10,7 @@ Other workloads (same JSON line; not run by default):
   small1k    the N=1,000 pair (subtree model / planted C_k), one batched call
   sparse1m   the N=2^20 CSR pair (reversed-PEO chordal / cycle-closing edges),
              the two graphs on two streams
+  sparse64k  the same recipe at N=65,536 (a small case for profiling)
   batch4096  4,096 graphs, N log-uniform in [16, 2048], one captured batch plan
   paper7     the paper's Section 7 families on GB300 beside the CPU oracle:
              cliques N = 1000..11000, dense random (p = 0.5), sparse random
@@ -146,10 +147,10 @@ def make_workload(name: str):
                                     "planted induced C_%d" % info["k"],
                         "n": g.n, "words_per_row": g.words, "graphs_per_step": 2,
                         "edges": [g.num_edges(), h.num_edges()], "bytes_per_graph": g.nbytes}
-    if name == "sparse1m":
-        g, h, info = gg.sparse_csr_pair()
-        return [g, h], {"workload": "CSR N=2^20 reversed-PEO chordal graph (cliques of size U{1..20}, shuffled ids) "
-                                    "+ copy with %d cycle-closing edges" % info["r"],
+    if name in ("sparse1m", "sparse64k"):
+        g, h, info = gg.sparse_csr_pair() if name == "sparse1m" else gg.sparse_csr_pair(n=1 << 16)
+        return [g, h], {"workload": "CSR N=%s reversed-PEO chordal graph (cliques of size U{1..20}, shuffled ids) "
+                                    "+ copy with %d cycle-closing edges" % ("2^20" if name == "sparse1m" else "65536", info["r"]),
                         "n": g.n, "graphs_per_step": 2, "edges": [g.num_edges(), h.num_edges()],
                         "bytes_per_graph": g.nbytes}
     if name == "batch4096":
@@ -571,7 +572,7 @@ def run_gpu(args):
     alg = sum(algorithmic_bytes(g) for g in graphs)
     phases = {"step_ms_p50": statistics.median(step_ms),
               "step_ms_p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]}
-    if wl in ("dense16k", "sparse1m"):
+    if wl in ("dense16k", "sparse1m", "sparse64k"):
         lex_ms = prof["lexbfs_ms"] / max(1, prof["lexbfs_launches"])
         chk_ms = prof["check_ms"] / max(1, prof["check_launches"])
         if wl == "dense16k":
@@ -656,7 +657,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dense16k",
-                    choices=["dense16k", "small1k", "sparse1m", "batch4096", "serve", "paper7"])
+                    choices=["dense16k", "small1k", "sparse1m", "sparse64k", "batch4096", "serve", "paper7"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -119,20 +119,25 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
     const int HEAD = n;
     int free_top = n - 1;
     int x = 0;
+    // the pivot's row, fetched ahead when the pivot is known early
+    int64_t pbeg = row_ptr[0], pend = row_ptr[1];
+    int pcol = (pend - pbeg <= 32 && pbeg + lane < pend) ? col[pbeg + lane] : -1;
     for (int i = 0; i < n; ++i) {
         // ---- number x (the first member of the top class f)
         const int f = s.cls[x];
         const int nx = s.vnext[x];
         const int fsize = s.csize[f] - 1;
+        // when f holds only x, the class after it becomes the top class
+        const int g_after = nx == kNone ? s.cnext[f] : kNone;
+        const int g_first = g_after != kNone ? s.cfirst[g_after] : kNone;
         if (lane == 0) {
             order[i] = x;
             if (pos) pos[x] = i;
             s.cls[x] = kNumberedCls;
             s.csize[f] = fsize;
             if (nx == kNone) {  // f held only x: drop it
-                const int cn = s.cnext[f];
-                s.cnext[HEAD] = cn;
-                if (cn != kNone) s.cprev[cn] = HEAD;
+                s.cnext[HEAD] = g_after;
+                if (g_after != kNone) s.cprev[g_after] = HEAD;
                 s.freel[free_top] = f;
             } else {
                 s.cfirst[f] = nx;
@@ -141,15 +146,35 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
         }
         if (nx == kNone) free_top += 1;
         __syncwarp();
-        const int64_t beg = row_ptr[x], end = row_ptr[x + 1];
+        const int64_t beg = pbeg, end = pend;
+        int next_x = -1;   // set when the single-chunk path finds the next pivot itself
 
         if (end - beg <= 32) {
             // ---- single chunk: everything in registers
             const int64_t j = beg + lane;
             const bool inrow = j < end;
-            const int y = inrow ? col[j] : -1;
+            const int y = inrow ? pcol : -1;
             const int c0 = inrow ? s.cls[y] : kNumberedCls;
             const bool valid = inrow && c0 != kNumberedCls;
+            // next pivot: the lowest moved vertex of the top class f; else f's
+            // next member; else (f emptied) the lowest moved vertex of the class
+            // after f, or its first member
+            {
+                const unsigned inf = __ballot_sync(kFull, valid && c0 == f);
+                if (inf) {
+                    next_x = __shfl_sync(kFull, y, __ffs(inf) - 1);
+                } else if (nx != kNone) {
+                    next_x = nx;
+                } else if (g_after != kNone) {
+                    const unsigned ing = __ballot_sync(kFull, valid && c0 == g_after);
+                    next_x = ing ? __shfl_sync(kFull, y, __ffs(ing) - 1) : g_first;
+                }
+                if (next_x >= 0) {   // fetch its row now, overlapping the rest of the step
+                    pbeg = row_ptr[next_x];
+                    pend = row_ptr[next_x + 1];
+                    pcol = (pend - pbeg <= 32 && pbeg + lane < pend) ? col[pbeg + lane] : -1;
+                }
+            }
             int op = 0, on = 0, csz = 0, cpv = 0;
             if (valid) {
                 op = s.vprev[y];
@@ -350,8 +375,14 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
         __syncwarp();
         // ---- next pivot: first member of the top class
         if (i + 1 < n) {
-            const int top = s.cnext[HEAD];
-            x = s.cfirst[top];
+            if (next_x < 0) {
+                const int top = s.cnext[HEAD];
+                next_x = s.cfirst[top];
+                pbeg = row_ptr[next_x];
+                pend = row_ptr[next_x + 1];
+                pcol = (pend - pbeg <= 32 && pbeg + lane < pend) ? col[pbeg + lane] : -1;
+            }
+            x = next_x;
         }
     }
 }
