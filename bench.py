@@ -169,6 +169,12 @@ def make_workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the current kernel (profiles/lexbfs_dense_n16384_pair.txt):
+# lexbfs_dense_kernel on the N=16,384 pair, 67.79 MB read + 1.87 MB written.
+NCU_TRAFFIC_BYTES = {"dense16k": 67.79e6 + 1.87e6}
+
+
 def algorithmic_bytes(g) -> int:
     """Bytes the method must read per graph: each pivot row once (LexBFS) plus
     row v and row p(v) per vertex (the check); CSR: row_ptr + col per pass,
@@ -588,7 +594,7 @@ def run_gpu(args):
         chk_gbs = chk_bytes / (chk_ms * 1e-3) / 1e9
         dom_share = prof["lexbfs_ms"] / max(1e-9, prof["lexbfs_ms"] + prof["check_ms"])
         roof = {"bound": "hbm", "kernel": f"{kernel} ({100 * dom_share:.1f}% of GPU time)", "achieved": lex_gbs,
-                "peak": hbm, "unit": "GB/s", "frac": lex_gbs / hbm, "traffic": None,
+                "peak": hbm, "unit": "GB/s", "frac": lex_gbs / hbm, "traffic": NCU_TRAFFIC_BYTES.get(wl),
                 "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": lex_bytes * per_launch}
         phases.update({"lexbfs_ms_per_launch": lex_ms, "check_ms_per_launch": chk_ms,
                        "lexbfs_ns_per_step": lex_ms * 1e6 / graphs[0].n, "check_gbs": chk_gbs,
