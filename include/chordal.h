@@ -135,6 +135,21 @@ int cg_chordal_test_dense_host(cg_context *ctx, int32_t n, int32_t words_per_row
                                cudaStream_t stream);
 
 /*
+ * Maximum Cardinality Search order of a dense graph (Section 5.2): each step
+ * numbers an unnumbered vertex with the most numbered neighbours, the lowest
+ * id among equals.  One CTA; per-vertex counts in shared memory (n <= 65520,
+ * larger n: CG_EINVAL).  order device int32[n]; pos device int32[n] or NULL.
+ */
+int cg_mcs_order_dense(cg_context *ctx, const cg_dense *g, int32_t *order, int32_t *pos, cudaStream_t stream);
+
+/* The chordality test with the MCS order (Theorem 5.2: G is chordal iff its
+ * MCS order is a perfect elimination order) and the same check and witness
+ * convention (the witness refers to the MCS order).  res device cg_result;
+ * order device int32[n] or NULL. */
+int cg_chordal_test_mcs_dense(cg_context *ctx, const cg_dense *g, cg_result *res, int32_t *order,
+                              cudaStream_t stream);
+
+/*
  * LexBFS order of a CSR graph (Section 4.2 in its O(N + M) form: each class a
  * list sorted by id, only the pivot's neighbours move).  One warp walks the n
  * steps with the partition state in the context workspace (about 84 B per

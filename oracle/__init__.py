@@ -7,8 +7,9 @@ imports it.
 
 Contents
 * ``oracle.c`` (compiled on demand to ``liboracle.so``): the O(N + M)
-  partition-refinement LexBFS with the lowest-id tie-break (Section 4.2) and
-  the perfect-elimination check with its canonical witness (Sections 5.3-5.4).
+  partition-refinement LexBFS with the lowest-id tie-break (Section 4.2), the
+  perfect-elimination check with its canonical witness (Sections 5.3-5.4), and
+  Maximum Cardinality Search with the same tie-break (Section 5.2).
 * ``reference.py``: slower restatements used to pin the C code — LexBFS by
   explicit labels (Section 4.1), the O(N^2) class-splitting form of Section
   4.2, Maximum Cardinality Search (Section 5.2) and the definition of a
@@ -57,6 +58,8 @@ def _load():
             lib.or_peo_check_dense.argtypes = [i32, i32, P, P, P, P]
             lib.or_chordal_test_csr.argtypes = [i32, P, P, P, P, P]
             lib.or_chordal_test_dense.argtypes = [i32, i32, P, P, P, P]
+            lib.or_mcs_csr.argtypes = [i32, P, P, P]
+            lib.or_mcs_dense.argtypes = [i32, i32, P, P]
             _lib = lib
     return _lib
 
@@ -110,6 +113,25 @@ def lexbfs(g) -> np.ndarray:
     if rc:
         raise ValueError(f"oracle lexbfs failed ({rc})")
     return order[:g.n]
+
+
+def mcs(g) -> np.ndarray:
+    """Maximum Cardinality Search order, lowest-id tie-break (Section 5.2)."""
+    order = np.zeros(max(g.n, 1), dtype=np.int32)
+    if _is_dense(g):
+        rows, words = _dense_args(g)
+        rc = _load().or_mcs_dense(g.n, words, _p(rows), _p(order))
+    else:
+        rp, col = _csr_args(g)
+        rc = _load().or_mcs_csr(g.n, _p(rp), _p(col), _p(order))
+    if rc:
+        raise ValueError(f"oracle mcs failed ({rc})")
+    return order[:g.n]
+
+
+def chordal_test_mcs(g) -> OracleResult:
+    """MCS order, then the perfect-elimination check (Theorem 5.2)."""
+    return peo_check(g, mcs(g))
 
 
 def peo_check(g, order) -> OracleResult:

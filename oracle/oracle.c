@@ -182,6 +182,79 @@ int or_lexbfs_dense(int32_t n, int32_t words, const uint32_t *rows, int32_t *ord
     return rc;
 }
 
+/* ------------------------------------------------------------------- MCS */
+
+/*
+ * Maximum Cardinality Search (Section 5.2): every unnumbered vertex carries the
+ * number of its numbered neighbours; each step numbers a vertex with the
+ * largest count, the lowest id among equals, and counts it at its unnumbered
+ * neighbours.  A binary max-heap of (count, -id) with lazy deletion: a vertex
+ * re-enters the heap on every increment and stale entries are skipped.
+ */
+typedef struct { int32_t label, v; } heap_item;
+
+static int item_above(heap_item a, heap_item b) {
+    return a.label > b.label || (a.label == b.label && a.v < b.v);
+}
+
+int or_mcs_csr(int32_t n, const int64_t *rp, const int32_t *col, int32_t *order) {
+    if (n < 0) return -1;
+    if (n == 0) return 0;
+    int64_t cap = n + (rp[n] > 0 ? rp[n] : 0) + 1;
+    heap_item *h = (heap_item *)malloc(sizeof(heap_item) * cap);
+    int32_t *label = (int32_t *)calloc(n, sizeof(int32_t));
+    uint8_t *numbered = (uint8_t *)calloc(n, 1);
+    if (!h || !label || !numbered) { free(h); free(label); free(numbered); return -2; }
+    int64_t hn = 0;
+    for (int32_t v = 0; v < n; ++v) {   /* equal labels: ascending ids form a valid heap */
+        h[hn].label = 0; h[hn].v = v; ++hn;
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t x = -1;
+        while (hn > 0) {
+            heap_item top = h[0];
+            /* pop */
+            h[0] = h[--hn];
+            for (int64_t k = 0;;) {
+                int64_t l = 2 * k + 1, r = l + 1, m = k;
+                if (l < hn && item_above(h[l], h[m])) m = l;
+                if (r < hn && item_above(h[r], h[m])) m = r;
+                if (m == k) break;
+                heap_item t = h[k]; h[k] = h[m]; h[m] = t; k = m;
+            }
+            if (!numbered[top.v] && top.label == label[top.v]) { x = top.v; break; }
+        }
+        if (x < 0) { free(h); free(label); free(numbered); return -3; }
+        order[i] = x;
+        numbered[x] = 1;
+        for (int64_t e = rp[x]; e < rp[x + 1]; ++e) {
+            int32_t y = col[e];
+            if (numbered[y]) continue;
+            label[y] += 1;
+            /* push (label[y], y) */
+            int64_t k = hn++;
+            h[k].label = label[y]; h[k].v = y;
+            while (k > 0) {
+                int64_t pidx = (k - 1) / 2;
+                if (!item_above(h[k], h[pidx])) break;
+                heap_item t = h[k]; h[k] = h[pidx]; h[pidx] = t; k = pidx;
+            }
+        }
+    }
+    free(h); free(label); free(numbered);
+    return 0;
+}
+
+int or_mcs_dense(int32_t n, int32_t words, const uint32_t *rows, int32_t *order) {
+    if (n < 0 || words < (n + 31) / 32) return -1;
+    if (n == 0) return 0;
+    int64_t *rp; int32_t *col;
+    if (dense_to_lists(n, words, rows, &rp, &col)) return -2;
+    int rc = or_mcs_csr(n, rp, col, order);
+    free(rp); free(col);
+    return rc;
+}
+
 /* ------------------------------------------------------- perfect elimination */
 
 static int adjacent_sorted(const int64_t *rp, const int32_t *col, int32_t a, int32_t b) {

@@ -85,6 +85,8 @@ SIGNATURES = {
     "cg_chordal_test_dense": ([P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_dense_host": ([P, I32, I32, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_batch": ([P, P, I32, P, P, P, P], ctypes.c_int),
+    "cg_mcs_order_dense": ([P, P, P, P, P], ctypes.c_int),
+    "cg_chordal_test_mcs_dense": ([P, P, P, P, P], ctypes.c_int),
     "cg_lexbfs_order_csr": ([P, P, P, P, P], ctypes.c_int),
     "cg_peo_check_csr": ([P, P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_csr": ([P, P, P, P, P], ctypes.c_int),
@@ -150,6 +152,8 @@ cg_peo_check_dense = _fn("cg_peo_check_dense")
 cg_chordal_test_dense = _fn("cg_chordal_test_dense")
 cg_chordal_test_dense_host = _fn("cg_chordal_test_dense_host")
 cg_chordal_test_batch = _fn("cg_chordal_test_batch")
+cg_mcs_order_dense = _fn("cg_mcs_order_dense")
+cg_chordal_test_mcs_dense = _fn("cg_chordal_test_mcs_dense")
 cg_lexbfs_order_csr = _fn("cg_lexbfs_order_csr")
 cg_peo_check_csr = _fn("cg_peo_check_csr")
 cg_chordal_test_csr = _fn("cg_chordal_test_csr")
@@ -236,6 +240,16 @@ def chordal_test_dense(ctx: Context, rows, n: int, res, order=None, stream=None)
     """res: CUDA int32 tensor [4] -> (chordal, v, p, u)."""
     d = dense_desc(rows, n)
     _check(cg_chordal_test_dense(ctx.handle, ctypes.byref(d), _ptr(res), _ptr(order), _stream(stream)))
+
+
+def mcs_order_dense(ctx: Context, rows, n: int, order, pos=None, stream=None):
+    d = dense_desc(rows, n)
+    _check(cg_mcs_order_dense(ctx.handle, ctypes.byref(d), _ptr(order), _ptr(pos), _stream(stream)))
+
+
+def chordal_test_mcs_dense(ctx: Context, rows, n: int, res, order=None, stream=None):
+    d = dense_desc(rows, n)
+    _check(cg_chordal_test_mcs_dense(ctx.handle, ctypes.byref(d), _ptr(res), _ptr(order), _stream(stream)))
 
 
 def peo_check_dense(ctx: Context, rows, n: int, order, res, parent=None, stream=None):

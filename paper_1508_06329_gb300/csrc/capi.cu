@@ -552,6 +552,53 @@ int cg_chordal_test_dense_host(cg_context *ctx, int32_t n, int32_t words_per_row
     return CG_OK;
 }
 
+namespace {
+// MCS order and (optionally) the check of one dense graph.
+int run_mcs_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int32_t *pos_out, cg_result *res,
+                  cudaStream_t stream) {
+    const int n = g->n;
+    Carve cv;
+    const size_t o_order = cv.take<int32_t>(n);
+    const size_t o_pos = cv.take<int32_t>(n);
+    const size_t o_parent = cv.take<int32_t>(n);
+    const size_t o_key = cv.take<unsigned long long>(1);
+    const size_t o_counter = cv.take<int>(1);
+    int rc;
+    if ((rc = ensure_ws(ctx, cv.off))) return rc;
+    int32_t *order = order_out ? order_out : at<int32_t>(ctx, o_order);
+    int32_t *pos = pos_out ? pos_out : at<int32_t>(ctx, o_pos);
+    int32_t *parent = at<int32_t>(ctx, o_parent);
+    const DenseDesc d = desc_of(g, 0, 0);
+    if (n > 0) {
+        PhaseTimer pt(ctx, &ctx->ev_lex, stream);
+        if ((rc = mcs_dense_launch(nullptr, d, 1, n, 1, order, pos, at<int>(ctx, o_counter), stream))) return rc;
+        ctx->launches += 1;
+    }
+    if (!res) return CG_OK;
+    PhaseTimer pt(ctx, &ctx->ev_check, stream);
+    unsigned long long *key = at<unsigned long long>(ctx, o_key);
+    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream)))
+        return rc;
+    ctx->launches += n > 0 ? 2 : 1;
+    return finalize_launch(nullptr, d, 1, key, order, parent, res, stream);
+}
+}  // namespace
+
+int cg_mcs_order_dense(cg_context *ctx, const cg_dense *g, int32_t *order, int32_t *pos, cudaStream_t stream) {
+    int rc;
+    if ((rc = check_ctx(ctx)) || (rc = check_dense(g))) return rc;
+    if (g->n > 0 && !order) return set_error(CG_EINVAL, "null order pointer");
+    return run_mcs_dense(ctx, g, order, pos, nullptr, stream);
+}
+
+int cg_chordal_test_mcs_dense(cg_context *ctx, const cg_dense *g, cg_result *res, int32_t *order,
+                              cudaStream_t stream) {
+    int rc;
+    if ((rc = check_ctx(ctx)) || (rc = check_dense(g))) return rc;
+    if (!res) return set_error(CG_EINVAL, "null result pointer");
+    return run_mcs_dense(ctx, g, order, nullptr, res, stream);
+}
+
 int cg_lexbfs_order_csr(cg_context *ctx, const cg_csr *g, int32_t *order, int32_t *pos, cudaStream_t stream) {
     int rc;
     if ((rc = check_ctx(ctx)) || (rc = check_csr(g))) return rc;

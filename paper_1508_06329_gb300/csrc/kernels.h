@@ -59,6 +59,10 @@ int fused_dense_launch(const FusedPlan &plan, const DenseDesc *descs, int count,
                        int32_t *pos, int32_t *parent, cg_result *res, int *work_counter, cudaStream_t stream);
 int fused_ctas_per_sm(const FusedPlan &plan);
 
+// ---- dense MCS (mcs_dense.cu): one CTA per graph, n <= 65520
+int mcs_dense_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, int ctas, int32_t *order,
+                     int32_t *pos, int *work_counter, cudaStream_t stream);
+
 // ---- CSR LexBFS (lexbfs_csr.cu): one warp per graph, state in `ws`
 size_t lexbfs_csr_workspace_bytes(int64_t n, int64_t max_deg);
 int lexbfs_csr_launch(int n, int64_t max_deg, const int64_t *row_ptr, const int32_t *col, int32_t *order,

@@ -183,3 +183,16 @@ def test_argument_errors(ctx):
     assert B.cg_chordal_test_dense(ctx.handle, B.ctypes.byref(bad), res.data_ptr(), None, None) == B.CG_EINVAL
     bad = B.cg_dense(200000, 6250, 0)
     assert B.cg_chordal_test_dense(ctx.handle, B.ctypes.byref(bad), res.data_ptr(), None, None) == B.CG_EINVAL
+
+
+@pytest.mark.parametrize("n", [65520, 65521])
+def test_variant_size_limits(ctx, n):
+    """The largest graph of the split-state variant (16-bit ids) and the first
+    one of the 32-bit-id variant; sparse graphs keep the oracle fast."""
+    g = gg.random_tree(n, n)
+    assert assert_parity(ctx, g).chordal == 1
+    h = g.copy()
+    # close one cycle: 0 - ... - far vertex
+    h.rows[0, (n - 1) >> 5] |= np.uint32(1 << ((n - 1) & 31))
+    h.rows[n - 1, 0] |= np.uint32(1)
+    assert_parity(ctx, h)

@@ -316,3 +316,40 @@ def test_planted_cycle_and_closing_edges_not_chordal():
         assert oracle.chordal_test(h).chordal == 0
         h2, pairs = gg.close_cycles_dense(g, 1 + s, 23 + s)
         assert len(pairs) == 1 + s and oracle.chordal_test(h2).chordal == 0
+
+
+# ----------------------------------------------------------------- MCS (Section 5.2)
+
+@pytest.mark.parametrize("n,p", [(10, 0.3), (60, 0.1), (150, 0.05), (200, 0.4)])
+def test_mcs_order_equals_definition(n, p):
+    """The heap-based C MCS equals the plain definition (largest count of
+    numbered neighbours, lowest id among equals)."""
+    for s in range(3):
+        adj = random_graph_adj(n, p, 71 * n + s)
+        assert oracle.mcs(csr_of(n, adj)).tolist() == R.mcs(adj)
+
+
+def test_mcs_verdict_theorem_5_2():
+    """Theorem 5.2: the MCS order is a PEO iff the graph is chordal (the
+    verdict is checked against the LexBFS test and against brute force)."""
+    rs = gg.rng_stream(808, 300)
+    for t in range(150):
+        n = 4 + int(rs[t]) % 60
+        if t % 2:
+            g = gg.subtree_dense(n, max(2, n // 3), int(rs[150 + t]))
+        else:
+            g = gg.random_dense(n, 0.05 + (t % 9) / 10.0, int(rs[150 + t]))
+        assert oracle.chordal_test_mcs(g).chordal == oracle.chordal_test(g).chordal
+    for n in range(4, 8):
+        for s in range(200):
+            g = gg.random_dense(n, 0.5, 9000 + 17 * n + s)
+            masks = [int(g.rows[i, 0]) for i in range(n)]
+            assert oracle.chordal_test_mcs(g).chordal == (0 if has_chordless_cycle(n, masks) else 1)
+
+
+def test_mcs_hand_c4_and_clique():
+    """C_4: 0 first; its neighbours 1 and 3 get count 1, 1 wins (lower id);
+    then 2 (count 1 from 1) ties with 3 (count 1), 2 wins; order 0,1,2,3.
+    A clique is visited in id order."""
+    assert oracle.mcs(gg.cycle(4)).tolist() == [0, 1, 2, 3]
+    assert oracle.mcs(gg.clique(9)).tolist() == list(range(9))
