@@ -20,8 +20,12 @@ Other workloads (same JSON line; not run by default):
              density U[0.01, 0.2], dense below N = 8,192, CSR above; arrival
              rate 0.8 x the measured saturation throughput; p50 / p99 latency
 
+`--order mcs` (dense16k, small1k) runs the same test with the Maximum
+Cardinality Search order (Section 5.2) instead of LexBFS: one graph per call,
+the two graphs on two streams.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--workload dense16k|small1k|sparse1m|batch4096]
+                    [--workload dense16k|small1k|sparse1m|batch4096|...] [--order lexbfs|mcs]
 
 Timing: inputs resident in HBM; before every timed step a 256 MiB buffer is
 written to flush L2; each step is bracketed by CUDA events on the launching
@@ -184,14 +188,20 @@ def algorithmic_bytes(g) -> int:
     return 3 * (8 * g.n + 4 * g.nnz) + 4 * g.nnz
 
 
-def oracle_rate(graphs, budget_s: float = 12.0, cap: int | None = None):
-    """Oracle tests/s on a bounded sample of the workload (single thread)."""
+def oracle_test_fn(order: str):
+    """The oracle's whole test for the chosen ordering (LexBFS or MCS)."""
     import oracle
+    return oracle.chordal_test_mcs if order == "mcs" else oracle.chordal_test
+
+
+def oracle_rate(graphs, budget_s: float = 12.0, cap: int | None = None, order: str = "lexbfs"):
+    """Oracle tests/s on a bounded sample of the workload (single thread)."""
+    test = oracle_test_fn(order)
     t0 = time.perf_counter()
     done = 0
     while True:
         for g in graphs:
-            oracle.chordal_test(g)
+            test(g)
             done += 1
             el = time.perf_counter() - t0
             if el >= budget_s or (cap and done >= cap):
@@ -229,20 +239,28 @@ def oracle_rate_all_cores(total: int = 4096):
 
 # --------------------------------------------------------------------------- reference arm
 
+def check_order_option(args):
+    if args.order == "mcs" and args.workload not in ("dense16k", "small1k", "paper7"):
+        raise SystemExit("--order mcs applies to the dense workloads dense16k, small1k and paper7")
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
     graphs, cfg = make_workload(args.workload)
-    import oracle
+    check_order_option(args)
+    if args.order == "mcs":
+        cfg = dict(cfg, order="MCS (Section 5.2)")
+    test = oracle_test_fn(args.order)
     sample = graphs if args.workload != "batch4096" else graphs[:512]
     for _ in range(args.warmup):
-        oracle.chordal_test(sample[0])
+        test(sample[0])
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
         for g in sample:
-            oracle.chordal_test(g)
+            test(g)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = len(sample) * args.steps / total
@@ -420,19 +438,38 @@ def run_paper7(args):
         oracle_ms = (time.perf_counter() - t0) * 1e3
         if got != want.witness or tuple(res.cpu().tolist()) != want.witness:
             raise SystemExit(f"parity failure on {fam} {label}")
+        # the same test with the MCS order (Section 5.2, Theorem 5.2)
+        B.chordal_test_mcs_dense(ctx, rows, g.n, res)
+        torch.cuda.synchronize()
+        mms = []
+        for _ in range(3):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            B.chordal_test_mcs_dense(ctx, rows, g.n, res)
+            b.record()
+            torch.cuda.synchronize()
+            mms.append(a.elapsed_time(b))
+        t0 = time.perf_counter()
+        want_mcs = oracle.chordal_test_mcs(g)
+        oracle_mcs_ms = (time.perf_counter() - t0) * 1e3
+        if tuple(res.cpu().tolist()) != want_mcs.witness or want_mcs.chordal != want.chordal:
+            raise SystemExit(f"MCS parity failure on {fam} {label}")
         gpu_ms = statistics.median(ms)
         gpu_total_ms += gpu_ms
         tests += 1
         table.append({"family": fam, "case": label, "n": g.n, "m": g.num_edges(), "chordal": want.chordal,
                       "gpu_ms": round(gpu_ms, 3), "gpu_e2e_ms": round(e2e_ms, 3), "oracle_ms": round(oracle_ms, 3),
-                      "oracle_over_gpu": round(oracle_ms / gpu_ms, 2)})
+                      "oracle_over_gpu": round(oracle_ms / gpu_ms, 2),
+                      "gpu_mcs_ms": round(statistics.median(mms), 3), "oracle_mcs_ms": round(oracle_mcs_ms, 3)})
     line = {"metric": METRIC, "value": tests / (gpu_total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 3,
             "warmup": 1, "ms_per_step": gpu_total_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32 bitsets / int32 (exact)", "data": "synthetic",
             "config": {"workload": "paper Section 7 families, one graph at a time (median of 3, L2 flushed)",
                        "gpu_ms": "LexBFS + check kernels, CUDA events",
                        "gpu_e2e_ms": "host rows -> device -> result (cg_chordal_test_dense_host)",
-                       "oracle_ms": "single-threaded C oracle, input already in memory"},
+                       "oracle_ms": "single-threaded C oracle, input already in memory",
+                       "gpu_mcs_ms / oracle_mcs_ms": "the same test with the MCS order (Section 5.2)"},
             "table": table}
     print(json.dumps(line))
     ctx.close()
@@ -455,7 +492,11 @@ def run_gpu(args):
     import oracle
 
     wl = args.workload
+    check_order_option(args)
+    mcs = args.order == "mcs"
     graphs, cfg = make_workload(wl)
+    if mcs:
+        cfg = dict(cfg, order="MCS (Section 5.2), one graph per stream")
     ngraph = len(graphs)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -467,7 +508,19 @@ def run_gpu(args):
         rows = [torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).to(dev) for g in graphs]
         batch = [(r, g.n) for r, g in zip(rows, graphs)]
         orders = torch.empty(max(1, sum(g.n for g in graphs)), dtype=torch.int32, device=dev)
-        if wl == "batch4096":
+        if mcs:
+            side = [torch.cuda.Stream(dev) for _ in graphs]
+            side_ctx = [ctx] + [B.Context(local) for _ in graphs[1:]]
+
+            def step():
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                for k, (r, g) in enumerate(zip(rows, graphs)):
+                    side[k].wait_event(ev)
+                    B.chordal_test_mcs_dense(side_ctx[k], r, g.n, res[k], None, side[k])
+                for s in side:
+                    stream.wait_stream(s)
+        elif wl == "batch4096":
             B.batch_autotune(ctx, batch)
             plan = B.BatchPlan(ctx, batch, res, orders)
 
@@ -499,11 +552,11 @@ def run_gpu(args):
     # parity guard on the timed configuration
     got = [tuple(r) for r in res.cpu().tolist()]
     if rank == 0:
-        want = [oracle.chordal_test(g).witness for g in graphs]
+        want = [oracle_test_fn(args.order)(g).witness for g in graphs]
         if got != want:
             raise SystemExit(f"parity failure in bench: {got[:4]} vs {want[:4]}")
 
-    all_ctx = side_ctx if not dense else [ctx]
+    all_ctx = side_ctx if (not dense or mcs) else [ctx]
     for c in all_ctx:
         c.read_profile()
         c.profile(True)
@@ -532,7 +585,22 @@ def run_gpu(args):
 
     # ---- end to end through the public API with host buffers
     e2e_steps = max(1, min(args.steps, 5 if wl != "sparse1m" else 1))
-    if dense and wl != "batch4096":
+    if mcs:
+        host_rows = [torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).pin_memory() for g in graphs]
+        host_res = torch.empty((ngraph, 4), dtype=torch.int32).pin_memory()
+        h2d = sum(g.nbytes for g in graphs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for hr, dr in zip(host_rows, rows):
+                dr.copy_(hr, non_blocking=True)
+            step()
+            host_res.copy_(res, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        out = [tuple(r) for r in host_res.tolist()]
+        e2e_path = "pinned host rows -> device, cg_chordal_test_mcs_dense per graph, results -> pinned host"
+    elif dense and wl != "batch4096":
         host_rows = [torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).pin_memory() for g in graphs]
         for g, hr in zip(graphs, host_rows):
             B.chordal_test_dense_host(ctx, hr, g.n, None, stream)
@@ -578,10 +646,14 @@ def run_gpu(args):
     alg = sum(algorithmic_bytes(g) for g in graphs)
     phases = {"step_ms_p50": statistics.median(step_ms),
               "step_ms_p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]}
-    if wl in ("dense16k", "sparse1m", "sparse64k"):
+    if wl in ("dense16k", "sparse1m", "sparse64k") or mcs:
         lex_ms = prof["lexbfs_ms"] / max(1, prof["lexbfs_launches"])
         chk_ms = prof["check_ms"] / max(1, prof["check_launches"])
-        if wl == "dense16k":
+        if mcs:
+            lex_bytes = graphs[0].n * graphs[0].words * 4           # each pivot row once, one graph per launch
+            chk_bytes = 2 * graphs[0].n * graphs[0].words * 4
+            per_launch = 1
+        elif wl == "dense16k":
             lex_bytes = sum(g.n * g.words * 4 for g in graphs)      # each pivot row once, both graphs per launch
             chk_bytes = sum(2 * g.n * g.words * 4 for g in graphs)
             per_launch = 1
@@ -590,11 +662,13 @@ def run_gpu(args):
             chk_bytes = 2 * (8 * graphs[0].n + 4 * graphs[0].nnz) + 4 * graphs[0].nnz
             per_launch = 1
         kernel = "lexbfs_dense_kernel" if wl == "dense16k" else "lexbfs_csr_kernel"
+        if mcs:
+            kernel = "mcs_dense_kernel"
         lex_gbs = lex_bytes / (lex_ms * 1e-3) / 1e9
         chk_gbs = chk_bytes / (chk_ms * 1e-3) / 1e9
         dom_share = prof["lexbfs_ms"] / max(1e-9, prof["lexbfs_ms"] + prof["check_ms"])
         roof = {"bound": "hbm", "kernel": f"{kernel} ({100 * dom_share:.1f}% of GPU time)", "achieved": lex_gbs,
-                "peak": hbm, "unit": "GB/s", "frac": lex_gbs / hbm, "traffic": NCU_TRAFFIC_BYTES.get(wl),
+                "peak": hbm, "unit": "GB/s", "frac": lex_gbs / hbm, "traffic": NCU_TRAFFIC_BYTES.get(wl + ("/mcs" if mcs else "")),
                 "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": lex_bytes * per_launch}
         phases.update({"lexbfs_ms_per_launch": lex_ms, "check_ms_per_launch": chk_ms,
                        "lexbfs_ns_per_step": lex_ms * 1e6 / graphs[0].n, "check_gbs": chk_gbs,
@@ -641,15 +715,15 @@ def run_gpu(args):
                                     "sample": f"all {done} graphs on {cores} processes (slowest worker's time); "
                                               f"single thread: {r1c:.0f} tests/s on {d1} graphs"}
         else:
-            rate, done, el = oracle_rate(graphs, budget_s=12.0 if wl != "sparse1m" else 4.0)
+            rate, done, el = oracle_rate(graphs, budget_s=12.0 if wl != "sparse1m" else 4.0, order=args.order)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"{done} tests of the workload's graphs, {el:.1f} s, "
-                                              "single-threaded C"}
+                                              "single-threaded C" + (" (MCS + check)" if mcs else "")}
     if rank == 0:
         print(json.dumps(line))
     if plan is not None:
         plan.close()
-    for c in (all_ctx if not dense else [ctx]):
+    for c in all_ctx:
         c.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -662,6 +736,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--order", default="lexbfs", choices=["lexbfs", "mcs"],
+                    help="vertex ordering of the test (dense workloads): LexBFS (default) or MCS")
     ap.add_argument("--workload", default="dense16k",
                     choices=["dense16k", "small1k", "sparse1m", "sparse64k", "batch4096", "serve", "paper7"])
     args = ap.parse_args()

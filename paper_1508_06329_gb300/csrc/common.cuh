@@ -28,6 +28,27 @@ int set_error(int status, const char *fmt, ...);
                                    cudaGetErrorString(e_));                                \
     } while (0)
 
+// Asks L2 to fetch [p, p + bytes) (bulk prefetch, no completion tracking).
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Spreads bulk L2 prefetches of a contiguous range over the CTA's threads.
+template <int T>
+__device__ __forceinline__ void prefetch_range_l2(const void *base, size_t bytes) {
+    constexpr uint32_t kChunk = 32768;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(base);
+    const uintptr_t a16 = (a + 15) & ~uintptr_t(15);
+    if (bytes <= (size_t)(a16 - a)) return;
+    size_t left = (bytes - (a16 - a)) & ~size_t(15);
+    const size_t chunks = (left + kChunk - 1) / kChunk;
+    for (size_t c = threadIdx.x; c < chunks; c += T) {
+        const size_t off = c * kChunk;
+        const uint32_t len = (uint32_t)((left - off) < kChunk ? (left - off) : kChunk);
+        prefetch_l2_bulk(reinterpret_cast<const void *>(a16 + off), len);
+    }
+}
+
 // Per-graph descriptor as the kernels see it (device memory).
 struct DenseDesc {
     const uint32_t *rows;   // n * words

@@ -144,27 +144,6 @@ __device__ __forceinline__ uint32_t row_word(const uint32_t *__restrict__ rows, 
     return w == wn - 1 ? (v & lastmask) : v;
 }
 
-// Asks L2 to fetch [p, p + bytes) (bulk prefetch, no completion tracking).
-__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Spreads bulk L2 prefetches of a contiguous range over the CTA's threads.
-template <int T>
-__device__ __forceinline__ void prefetch_range_l2(const void *base, size_t bytes) {
-    constexpr uint32_t kChunk = 32768;
-    const uintptr_t a = reinterpret_cast<uintptr_t>(base);
-    const uintptr_t a16 = (a + 15) & ~uintptr_t(15);
-    if (bytes <= (size_t)(a16 - a)) return;
-    size_t left = (bytes - (a16 - a)) & ~size_t(15);
-    const size_t chunks = (left + kChunk - 1) / kChunk;
-    for (size_t c = threadIdx.x; c < chunks; c += T) {
-        const size_t off = c * kChunk;
-        const uint32_t len = (uint32_t)((left - off) < kChunk ? (left - off) : kChunk);
-        prefetch_l2_bulk(reinterpret_cast<const void *>(a16 + off), len);
-    }
-}
-
 // One CTA computes the LexBFS order of one graph.  rows/stride address the
 // adjacency (global memory, or a compact shared-memory copy).  parent may be
 // null; otherwise parent[v] receives p(v) (or -1 when v has no earlier
