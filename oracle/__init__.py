@@ -7,7 +7,8 @@ imports it.
 
 Contents
 * ``oracle.c`` (compiled on demand to ``liboracle.so``): the O(N + M)
-  partition-refinement LexBFS with the lowest-id tie-break (Section 4.2), the
+  partition-refinement LexBFS with the lowest-id tie-break (Section 4.2) or a
+  caller-given tie-break rank and start vertex (multi-sweep LexBFS), the
   perfect-elimination check with its canonical witness (Sections 5.3-5.4), and
   Maximum Cardinality Search with the same tie-break (Section 5.2).
 * ``reference.py``: slower restatements used to pin the C code — LexBFS by
@@ -58,6 +59,8 @@ def _load():
             lib.or_peo_check_dense.argtypes = [i32, i32, P, P, P, P]
             lib.or_chordal_test_csr.argtypes = [i32, P, P, P, P, P]
             lib.or_chordal_test_dense.argtypes = [i32, i32, P, P, P, P]
+            lib.or_lexbfs_rank_csr.argtypes = [i32, P, P, P, i32, P]
+            lib.or_lexbfs_rank_dense.argtypes = [i32, i32, P, P, i32, P]
             lib.or_mcs_csr.argtypes = [i32, P, P, P]
             lib.or_mcs_dense.argtypes = [i32, i32, P, P]
             _lib = lib
@@ -113,6 +116,34 @@ def lexbfs(g) -> np.ndarray:
     if rc:
         raise ValueError(f"oracle lexbfs failed ({rc})")
     return order[:g.n]
+
+
+def lexbfs_tiebreak(g, rank=None, start: int = -1) -> np.ndarray:
+    """LexBFS whose ties go to the smallest rank[v] (a permutation of
+    0..n-1; None = the vertex id), with `start` (if >= 0) numbered first: the
+    sweep that multi-sweep LexBFS repeats (Section 4.2's refinement started
+    from the class ordered by rank)."""
+    order = np.zeros(max(g.n, 1), dtype=np.int32)
+    rk = None if rank is None else np.ascontiguousarray(rank, dtype=np.int32)
+    rp_ = ctypes.c_void_p(0) if rk is None else _p(rk)
+    if _is_dense(g):
+        rows, words = _dense_args(g)
+        rc = _load().or_lexbfs_rank_dense(g.n, words, _p(rows), rp_, int(start), _p(order))
+    else:
+        rp, col = _csr_args(g)
+        rc = _load().or_lexbfs_rank_csr(g.n, _p(rp), _p(col), rp_, int(start), _p(order))
+    if rc:
+        raise ValueError(f"oracle lexbfs_tiebreak failed ({rc})")
+    return order[:g.n]
+
+
+def lexbfs_plus(g, prev_order, start: int = -1) -> np.ndarray:
+    """LexBFS+ of a previous sweep: ties go to the vertex that comes latest in
+    prev_order (rank = n - 1 - position in prev_order)."""
+    prev = np.asarray(prev_order, dtype=np.int64)
+    rank = np.empty(g.n, dtype=np.int32)
+    rank[prev] = g.n - 1 - np.arange(g.n)
+    return lexbfs_tiebreak(g, rank, start)
 
 
 def mcs(g) -> np.ndarray:

@@ -109,9 +109,11 @@ static int class_detach(lexbfs_state *s, int32_t c, int32_t y) {
     return 0;
 }
 
-int or_lexbfs_csr(int32_t n, const int64_t *rp, const int32_t *col, int32_t *order) {
-    if (n < 0) return -1;
-    if (n == 0) return 0;
+/* Partition refinement from the initial sequence seq (one class holding the
+ * vertices in that order).  Each row of (rp, col) must list the neighbours in
+ * the order of their positions in seq, so that moved vertices keep that order
+ * inside every class. */
+static int hmpv_lexbfs(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *seq, int32_t *order) {
     lexbfs_state s;
     int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)n * 10 + 64);
     if (!mem) return -2;
@@ -121,13 +123,14 @@ int or_lexbfs_csr(int32_t n, const int64_t *rp, const int32_t *col, int32_t *ord
     s.freestack = mem + 9 * (size_t)n;
     uint8_t *numbered = (uint8_t *)calloc(n, 1);
     if (!numbered) { free(mem); return -2; }
-    /* one class (id 0) holding 0..n-1 in id order */
-    for (int32_t v = 0; v < n; ++v) {
-        s.vprev[v] = v - 1;
-        s.vnext[v] = v + 1 < n ? v + 1 : -1;
+    /* one class (id 0) holding the vertices in the order of seq */
+    for (int32_t k = 0; k < n; ++k) {
+        int32_t v = seq[k];
+        s.vprev[v] = k > 0 ? seq[k - 1] : -1;
+        s.vnext[v] = k + 1 < n ? seq[k + 1] : -1;
         s.cls[v] = 0;
     }
-    s.cfirst[0] = 0; s.clast[0] = n - 1; s.cnext[0] = s.cprev[0] = -1; s.cstamp[0] = -1;
+    s.cfirst[0] = seq[0]; s.clast[0] = seq[n - 1]; s.cnext[0] = s.cprev[0] = -1; s.cstamp[0] = -1;
     s.chead = 0;
     s.nfree = 0;
     for (int32_t c = n - 1; c >= 1; --c) s.freestack[s.nfree++] = c;
@@ -170,6 +173,72 @@ int or_lexbfs_csr(int32_t n, const int64_t *rp, const int32_t *col, int32_t *ord
     free(numbered);
     free(mem);
     return 0;
+}
+
+int or_lexbfs_csr(int32_t n, const int64_t *rp, const int32_t *col, int32_t *order) {
+    if (n < 0) return -1;
+    if (n == 0) return 0;
+    int32_t *seq = (int32_t *)malloc(sizeof(int32_t) * n);
+    if (!seq) return -2;
+    for (int32_t v = 0; v < n; ++v) seq[v] = v;   /* rows are sorted by id already */
+    int rc = hmpv_lexbfs(n, rp, col, seq, order);
+    free(seq);
+    return rc;
+}
+
+/*
+ * LexBFS with a caller-given tie-break (the building block of multi-sweep
+ * LexBFS): among the unnumbered vertices with the lexicographically largest
+ * label, the one with the smallest rank[v] is numbered; start >= 0 is numbered
+ * first.  rank must be a permutation of 0..n-1 (else -4).  This is Section
+ * 4.2's refinement started from the single class ordered by (start first,
+ * then rank), with every neighbour list taken in that same order.
+ */
+static const int32_t *g_sort_key;
+static int by_key(const void *a, const void *b) {
+    int32_t ka = g_sort_key[*(const int32_t *)a], kb = g_sort_key[*(const int32_t *)b];
+    return (ka > kb) - (ka < kb);
+}
+
+int or_lexbfs_rank_csr(int32_t n, const int64_t *rp, const int32_t *col, const int32_t *rank, int32_t start,
+                       int32_t *order) {
+    if (n < 0 || start >= n) return -1;
+    if (n == 0) return 0;
+    int32_t *key = (int32_t *)malloc(sizeof(int32_t) * n);
+    int32_t *seq = (int32_t *)malloc(sizeof(int32_t) * n);
+    int32_t *col2 = (int32_t *)malloc(sizeof(int32_t) * (rp[n] > 0 ? rp[n] : 1));
+    if (!key || !seq || !col2) { free(key); free(seq); free(col2); return -2; }
+    for (int32_t v = 0; v < n; ++v) seq[v] = -1;
+    for (int32_t v = 0; v < n; ++v) {
+        int32_t r = rank ? rank[v] : v;
+        if (r < 0 || r >= n || seq[r] >= 0) { free(key); free(seq); free(col2); return -4; }
+        seq[r] = v;
+        key[v] = v == start ? -1 : r;
+    }
+    if (start >= 0) {   /* move start to the front of the sequence */
+        int32_t r = rank ? rank[start] : start;
+        for (int32_t k = r; k > 0; --k) seq[k] = seq[k - 1];
+        seq[0] = start;
+    }
+    g_sort_key = key;
+    for (int32_t v = 0; v < n; ++v) {
+        memcpy(col2 + rp[v], col + rp[v], sizeof(int32_t) * (size_t)(rp[v + 1] - rp[v]));
+        qsort(col2 + rp[v], (size_t)(rp[v + 1] - rp[v]), sizeof(int32_t), by_key);
+    }
+    int rc = hmpv_lexbfs(n, rp, col2, seq, order);
+    free(key); free(seq); free(col2);
+    return rc;
+}
+
+int or_lexbfs_rank_dense(int32_t n, int32_t words, const uint32_t *rows, const int32_t *rank, int32_t start,
+                         int32_t *order) {
+    if (n < 0 || words < (n + 31) / 32) return -1;
+    if (n == 0) return 0;
+    int64_t *rp; int32_t *col;
+    if (dense_to_lists(n, words, rows, &rp, &col)) return -2;
+    int rc = or_lexbfs_rank_csr(n, rp, col, rank, start, order);
+    free(rp); free(col);
+    return rc;
 }
 
 int or_lexbfs_dense(int32_t n, int32_t words, const uint32_t *rows, int32_t *order) {

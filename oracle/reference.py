@@ -9,7 +9,7 @@ from __future__ import annotations
 import numpy as np
 
 
-def lexbfs_labels(adj) -> list[int]:
+def lexbfs_labels(adj, prefer=None) -> list[int]:
     """LexBFS with explicit string labels (Section 4.1).
 
     Every vertex starts with the empty label.  In step i (1-based) the vertex x
@@ -17,7 +17,7 @@ def lexbfs_labels(adj) -> list[int]:
     is appended to the label of each unnumbered neighbour of x (the printed
     update names label_x; it is the neighbour's label that grows).  Labels are
     compared as sequences, a proper prefix being smaller; ties go to the
-    lowest vertex id.
+    lowest vertex id, or to the lowest prefer[v] when prefer is given.
     """
     n = len(adj)
     nbrs = [set(a) for a in adj]
@@ -25,7 +25,8 @@ def lexbfs_labels(adj) -> list[int]:
     numbered = [False] * n
     order = []
     for i in range(1, n + 1):
-        x = max((v for v in range(n) if not numbered[v]), key=lambda v: (label[v], -v))
+        x = max((v for v in range(n) if not numbered[v]),
+                key=lambda v: (label[v], -(v if prefer is None else prefer[v])))
         numbered[x] = True
         order.append(x)
         for y in nbrs[x]:
@@ -70,7 +71,8 @@ def mcs(adj) -> list[int]:
     numbered = [False] * n
     order = []
     for _ in range(n):
-        x = max((v for v in range(n) if not numbered[v]), key=lambda v: (label[v], -v))
+        x = max((v for v in range(n) if not numbered[v]),
+                key=lambda v: (label[v], -(v if prefer is None else prefer[v])))
         numbered[x] = True
         order.append(x)
         for y in nbrs[x]:

@@ -353,3 +353,75 @@ def test_mcs_hand_c4_and_clique():
     A clique is visited in id order."""
     assert oracle.mcs(gg.cycle(4)).tolist() == [0, 1, 2, 3]
     assert oracle.mcs(gg.clique(9)).tolist() == list(range(9))
+
+
+# ----------------------------------------------------------------- multi-sweep LexBFS (tie-break rank, start)
+
+def _prefer(rank, start):
+    pref = list(int(r) for r in rank)
+    if start >= 0:
+        pref[start] = -1
+    return pref
+
+
+@pytest.mark.parametrize("n,p", [(12, 0.3), (60, 0.1), (120, 0.05), (150, 0.4)])
+def test_tiebreak_order_equals_explicit_labels(n, p):
+    """A caller-given tie-break: the refinement started from the class ordered
+    by rank equals explicit-label LexBFS whose ties go to the lowest rank, with
+    the start vertex first."""
+    for s in range(3):
+        adj = random_graph_adj(n, p, 31 * n + s)
+        rank = np.random.default_rng(n + s).permutation(n).astype(np.int32)
+        start = -1 if s == 0 else (7 * s) % n
+        g = csr_of(n, adj)
+        got = oracle.lexbfs_tiebreak(g, rank, start).tolist()
+        assert got == R.lexbfs_labels(adj, _prefer(rank, start))
+        assert R.lb_violations(adj, got) == 0
+        if start >= 0:
+            assert got[0] == start
+        # the dense entry agrees with the CSR one
+        assert oracle.lexbfs_tiebreak(gg.csr_to_dense(g), rank, start).tolist() == got
+
+
+def test_tiebreak_identity_and_relabelling():
+    """rank = id gives the plain LexBFS; a LexBFS with tie-break rank equals
+    the plain LexBFS of the graph relabelled by rank, mapped back."""
+    g = gg.random_dense(200, 0.08, 44)
+    assert np.array_equal(oracle.lexbfs_tiebreak(g), oracle.lexbfs(g))
+    assert np.array_equal(oracle.lexbfs_tiebreak(g, np.arange(200, dtype=np.int32)), oracle.lexbfs(g))
+    rank = np.random.default_rng(5).permutation(200).astype(np.int32)
+    h = gg.relabel_dense(g, rank)            # vertex v becomes rank[v]
+    inv = np.empty(200, np.int64)
+    inv[rank] = np.arange(200)
+    assert np.array_equal(oracle.lexbfs_tiebreak(g, rank), inv[oracle.lexbfs(h)])
+
+
+def test_tiebreak_rejects_non_permutation():
+    g = gg.random_dense(20, 0.2, 1)
+    rank = np.arange(20, dtype=np.int32)
+    rank[3] = 4
+    with pytest.raises(ValueError):
+        oracle.lexbfs_tiebreak(g, rank)
+
+
+def test_lexbfs_plus_sweeps():
+    """LexBFS+ (ties to the vertex latest in the previous sweep): its first
+    vertex is the previous sweep's last one; every sweep is a LexBFS order
+    (property LB), and on chordal graphs a perfect elimination order
+    (Theorem 5.1), so its last vertex is simplicial."""
+    for seed in range(4):
+        for g in (gg.subtree_dense(90, 30, 600 + seed), gg.interval_graph(80, 700 + seed),
+                  gg.random_dense(70, 0.15, 800 + seed)):
+            adj = gg.adjacency_lists(g)
+            prev = oracle.lexbfs(g)
+            for _ in range(3):
+                plus = oracle.lexbfs_plus(g, prev)
+                assert plus[0] == prev[-1]
+                assert R.lb_violations(adj, plus.tolist()) == 0
+                res = oracle.peo_check(g, plus)
+                assert res.chordal == oracle.chordal_test(g).chordal
+                if res.chordal:
+                    last = int(plus[-1])
+                    nb = adj[last]
+                    assert all(b in set(adj[a]) for a in nb for b in nb if a != b)
+                prev = plus
