@@ -71,8 +71,7 @@ def mcs(adj) -> list[int]:
     numbered = [False] * n
     order = []
     for _ in range(n):
-        x = max((v for v in range(n) if not numbered[v]),
-                key=lambda v: (label[v], -(v if prefer is None else prefer[v])))
+        x = max((v for v in range(n) if not numbered[v]), key=lambda v: (label[v], -v))
         numbered[x] = True
         order.append(x)
         for y in nbrs[x]:
