@@ -21,7 +21,7 @@ Other workloads (same JSON line; not run by default):
              rate 0.8 x the measured saturation throughput; p50 / p99 latency
 
 `--order mcs` (dense16k, small1k) runs the same test with the Maximum
-Cardinality Search order (Section 5.2) instead of LexBFS: one graph per call,
+Cardinality Search order (Section 5.1) instead of LexBFS: one graph per call,
 the two graphs on two streams.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
@@ -251,7 +251,7 @@ def run_reference(args):
     graphs, cfg = make_workload(args.workload)
     check_order_option(args)
     if args.order == "mcs":
-        cfg = dict(cfg, order="MCS (Section 5.2)")
+        cfg = dict(cfg, order="MCS (Section 5.1)")
     test = oracle_test_fn(args.order)
     sample = graphs if args.workload != "batch4096" else graphs[:512]
     for _ in range(args.warmup):
@@ -438,7 +438,7 @@ def run_paper7(args):
         oracle_ms = (time.perf_counter() - t0) * 1e3
         if got != want.witness or tuple(res.cpu().tolist()) != want.witness:
             raise SystemExit(f"parity failure on {fam} {label}")
-        # the same test with the MCS order (Section 5.2, Theorem 5.2)
+        # the same test with the MCS order (Section 5.1, Theorem 5.2)
         B.chordal_test_mcs_dense(ctx, rows, g.n, res)
         torch.cuda.synchronize()
         mms = []
@@ -469,7 +469,7 @@ def run_paper7(args):
                        "gpu_ms": "LexBFS + check kernels, CUDA events",
                        "gpu_e2e_ms": "host rows -> device -> result (cg_chordal_test_dense_host)",
                        "oracle_ms": "single-threaded C oracle, input already in memory",
-                       "gpu_mcs_ms / oracle_mcs_ms": "the same test with the MCS order (Section 5.2)"},
+                       "gpu_mcs_ms / oracle_mcs_ms": "the same test with the MCS order (Section 5.1)"},
             "table": table}
     print(json.dumps(line))
     ctx.close()
@@ -496,7 +496,7 @@ def run_gpu(args):
     mcs = args.order == "mcs"
     graphs, cfg = make_workload(wl)
     if mcs:
-        cfg = dict(cfg, order="MCS (Section 5.2), one graph per stream")
+        cfg = dict(cfg, order="MCS (Section 5.1), one graph per stream")
     ngraph = len(graphs)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)

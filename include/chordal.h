@@ -4,7 +4,7 @@
  *
  * The test has two parts (Section 6): a LexBFS order computed by partition
  * refinement (Sections 4.2 and 6.1), then the perfect-elimination check of
- * that order (Sections 5.3 and 6.2).  G is chordal iff the LexBFS order is a
+ * that order (Sections 5.2 and 6.2).  G is chordal iff the LexBFS order is a
  * perfect elimination order (Theorem 5.1).
  *
  * Conventions used by every entry point
@@ -22,7 +22,7 @@
  *     leaves the choice open, Section 6.1; this fixes one LexBFS order).
  *   - Witness: when the graph is not chordal, v is the vertex with the
  *     smallest order index whose earlier neighbourhood LN_v is not a clique
- *     (the "first such node" of Section 5.4), p = p(v) is its neighbour with
+ *     (the "first such node" of Section 5.3), p = p(v) is its neighbour with
  *     the largest order index below v's, and u is the smallest id in
  *     (LN_v - {p}) \ N(p).  When chordal, v = p = u = -1.
  *   - Pointers named "device" are CUDA device pointers owned by the caller;
@@ -109,7 +109,29 @@ int cg_lexbfs_order_dense(cg_context *ctx, const cg_dense *g, int32_t *order, in
                           cudaStream_t stream);
 
 /*
- * Perfect-elimination check of a caller-given order (Sections 5.3 and 6.2):
+ * One sweep of multi-sweep LexBFS on a dense graph: LexBFS (Section 4.2) in
+ * which, among the unnumbered vertices with the lexicographically largest
+ * label, the one chosen is
+ *   CG_TIE_ID       the lowest vertex id (tiebreak unused; as above),
+ *   CG_TIE_RANK     the one with the smallest tiebreak[v]; tiebreak is a
+ *                   device int32[n] permutation of 0..n-1,
+ *   CG_TIE_LAST_IN  the one latest in tiebreak, a device int32[n] vertex
+ *                   order (a previous sweep): LexBFS+ of that sweep;
+ * and start (-1 = none, else 0 <= start < n) is numbered first.  This is
+ * the building block of the multi-sweep algorithms that use LexBFS beyond the
+ * chordality test (interval and co-comparability recognition, Section 3.2;
+ * the parallel interval test named as future work in Section 8).
+ * The graph is relabelled on the GPU (workspace: n * ceil(n/32) * 4 bytes
+ * more) and the dense LexBFS runs on the copy.  n <= 131072.  A tiebreak
+ * array that is not a permutation gives an unspecified order; with
+ * cfg.validate set it returns CG_EINVAL instead (synchronising the stream).
+ */
+enum { CG_TIE_ID = 0, CG_TIE_RANK = 1, CG_TIE_LAST_IN = 2 };
+int cg_lexbfs_sweep_dense(cg_context *ctx, const cg_dense *g, int32_t kind, const int32_t *tiebreak, int32_t start,
+                          int32_t *order, int32_t *pos, cudaStream_t stream);
+
+/*
+ * Perfect-elimination check of a caller-given order (Sections 5.2 and 6.2):
  * p(v) = the neighbour of v with the largest order index below v's, then
  * LN_v - {p(v)} ⊆ N(p(v)) for every v.  The order need not be a LexBFS
  * order; for a LexBFS order the verdict is the chordality verdict.
@@ -135,7 +157,7 @@ int cg_chordal_test_dense_host(cg_context *ctx, int32_t n, int32_t words_per_row
                                cudaStream_t stream);
 
 /*
- * Maximum Cardinality Search order of a dense graph (Section 5.2): each step
+ * Maximum Cardinality Search order of a dense graph (Section 5.1): each step
  * numbers an unnumbered vertex with the most numbered neighbours, the lowest
  * id among equals.  One CTA; per-vertex counts in shared memory (n <= 65520,
  * larger n: CG_EINVAL).  order device int32[n]; pos device int32[n] or NULL.
@@ -161,7 +183,7 @@ int cg_chordal_test_mcs_dense(cg_context *ctx, const cg_dense *g, cg_result *res
 int cg_lexbfs_order_csr(cg_context *ctx, const cg_csr *g, int32_t *order, int32_t *pos, cudaStream_t stream);
 
 /* Perfect-elimination check of a caller-given order on a CSR graph (Sections
- * 5.3, 6.2): LN_v - {p(v)} ⊆ N(p(v)) by binary search in p's sorted row.
+ * 5.2, 6.2): LN_v - {p(v)} ⊆ N(p(v)) by binary search in p's sorted row.
  *   order device int32[n] permutation; parent device int32[n] or NULL;
  *   res device cg_result */
 int cg_peo_check_csr(cg_context *ctx, const cg_csr *g, const int32_t *order, int32_t *parent, cg_result *res,

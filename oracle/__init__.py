@@ -9,11 +9,11 @@ Contents
 * ``oracle.c`` (compiled on demand to ``liboracle.so``): the O(N + M)
   partition-refinement LexBFS with the lowest-id tie-break (Section 4.2) or a
   caller-given tie-break rank and start vertex (multi-sweep LexBFS), the
-  perfect-elimination check with its canonical witness (Sections 5.3-5.4), and
-  Maximum Cardinality Search with the same tie-break (Section 5.2).
+  perfect-elimination check with its canonical witness (Sections 5.2-5.3), and
+  Maximum Cardinality Search with the same tie-break (Section 5.1).
 * ``reference.py``: slower restatements used to pin the C code — LexBFS by
   explicit labels (Section 4.1), the O(N^2) class-splitting form of Section
-  4.2, Maximum Cardinality Search (Section 5.2) and the definition of a
+  4.2, Maximum Cardinality Search (Section 5.1) and the definition of a
   perfect elimination order (Section 3.1).
 
 Result convention: ``(chordal, v, p, u)``; when chordal is 1 the witness is
@@ -147,7 +147,7 @@ def lexbfs_plus(g, prev_order, start: int = -1) -> np.ndarray:
 
 
 def mcs(g) -> np.ndarray:
-    """Maximum Cardinality Search order, lowest-id tie-break (Section 5.2)."""
+    """Maximum Cardinality Search order, lowest-id tie-break (Section 5.1)."""
     order = np.zeros(max(g.n, 1), dtype=np.int32)
     if _is_dense(g):
         rows, words = _dense_args(g)
@@ -166,7 +166,7 @@ def chordal_test_mcs(g) -> OracleResult:
 
 
 def peo_check(g, order) -> OracleResult:
-    """Perfect-elimination check of a given order (Sections 5.3-5.4)."""
+    """Perfect-elimination check of a given order (Sections 5.2-5.3)."""
     order = np.ascontiguousarray(order, dtype=np.int32)
     parent = np.zeros(max(g.n, 1), dtype=np.int32)
     res = np.zeros(4, dtype=np.int32)

@@ -15,12 +15,12 @@
  *      appended to the tail of the new class, so every class stays sorted by
  *      id and "first vertex of the first class" is the lowest id among the
  *      vertices with the lexicographically largest label.
- *   2. The perfect-elimination check (Section 5.3, "chordalityTest"): for
+ *   2. The perfect-elimination check (Section 5.2, "chordalityTest"): for
  *      each v, p(v) is the neighbour of v with the largest order index below
  *      that of v, and the test is LN_v - {p(v)} ⊆ N(p(v)).  Every member of
  *      LN_v - {p} precedes p, so membership in N(p) and in LN_p coincide.
  *   3. The witness: v* = the violating vertex with the smallest order index
- *      (the "first such node" of the correctness proof in Section 5.4),
+ *      (the "first such node" of the correctness proof in Section 5.3),
  *      p* = p(v*), u* = the smallest id in (LN_v* - {p*}) \ N(p*).
  * Result array: {chordal, v*, p*, u*}; (v*, p*, u*) = -1 when chordal.
  * Complexity O(N + M) (plus a binary search per tested edge).
@@ -254,7 +254,7 @@ int or_lexbfs_dense(int32_t n, int32_t words, const uint32_t *rows, int32_t *ord
 /* ------------------------------------------------------------------- MCS */
 
 /*
- * Maximum Cardinality Search (Section 5.2): every unnumbered vertex carries the
+ * Maximum Cardinality Search (Section 5.1): every unnumbered vertex carries the
  * number of its numbered neighbours; each step numbers a vertex with the
  * largest count, the lowest id among equals, and counts it at its unnumbered
  * neighbours.  A binary max-heap of (count, -id) with lazy deletion: a vertex

@@ -62,7 +62,7 @@ def lexbfs_classes(adj) -> list[int]:
 
 
 def mcs(adj) -> list[int]:
-    """Maximum Cardinality Search (Section 5.2): the label of a vertex is the
+    """Maximum Cardinality Search (Section 5.1): the label of a vertex is the
     number of its already-numbered neighbours; the largest label is taken
     next, ties to the lowest id."""
     n = len(adj)

@@ -85,6 +85,7 @@ SIGNATURES = {
     "cg_chordal_test_dense": ([P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_dense_host": ([P, I32, I32, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_batch": ([P, P, I32, P, P, P, P], ctypes.c_int),
+    "cg_lexbfs_sweep_dense": ([P, P, ctypes.c_int32, P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "cg_mcs_order_dense": ([P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_mcs_dense": ([P, P, P, P, P], ctypes.c_int),
     "cg_lexbfs_order_csr": ([P, P, P, P, P], ctypes.c_int),
@@ -152,6 +153,7 @@ cg_peo_check_dense = _fn("cg_peo_check_dense")
 cg_chordal_test_dense = _fn("cg_chordal_test_dense")
 cg_chordal_test_dense_host = _fn("cg_chordal_test_dense_host")
 cg_chordal_test_batch = _fn("cg_chordal_test_batch")
+cg_lexbfs_sweep_dense = _fn("cg_lexbfs_sweep_dense")
 cg_mcs_order_dense = _fn("cg_mcs_order_dense")
 cg_chordal_test_mcs_dense = _fn("cg_chordal_test_mcs_dense")
 cg_lexbfs_order_csr = _fn("cg_lexbfs_order_csr")
@@ -240,6 +242,21 @@ def chordal_test_dense(ctx: Context, rows, n: int, res, order=None, stream=None)
     """res: CUDA int32 tensor [4] -> (chordal, v, p, u)."""
     d = dense_desc(rows, n)
     _check(cg_chordal_test_dense(ctx.handle, ctypes.byref(d), _ptr(res), _ptr(order), _stream(stream)))
+
+
+TIE_ID, TIE_RANK, TIE_LAST_IN = 0, 1, 2
+
+
+def lexbfs_sweep_dense(ctx: Context, rows, n: int, order, pos=None, kind: int = TIE_ID, tiebreak=None,
+                       start: int = -1, stream=None):
+    d = dense_desc(rows, n)
+    _check(cg_lexbfs_sweep_dense(ctx.handle, ctypes.byref(d), kind, _ptr(tiebreak), start, _ptr(order), _ptr(pos),
+                                 _stream(stream)))
+
+
+def lexbfs_plus_dense(ctx: Context, rows, n: int, prev_order, order, pos=None, start: int = -1, stream=None):
+    """LexBFS+ of a previous sweep: ties go to the vertex latest in prev_order."""
+    lexbfs_sweep_dense(ctx, rows, n, order, pos, TIE_LAST_IN, prev_order, start, stream)
 
 
 def mcs_order_dense(ctx: Context, rows, n: int, order, pos=None, stream=None):

@@ -3,7 +3,7 @@
 //
 // Each CTA takes graphs from an atomic counter (graphs pre-sorted largest
 // first by the host), runs the partition-refinement LexBFS of
-// lexbfs_dense.cuh, then the perfect-elimination check of Sections 5.3 / 6.2
+// lexbfs_dense.cuh, then the perfect-elimination check of Sections 5.2 / 6.2
 // on the same graph: its warps take vertices v, read p = p(v) (recorded by
 // the search) and scan row_v & ~row_p for an earlier vertex other than p; the
 // CTA keeps the first violation in order with a shared 64-bit atomicMin on

@@ -486,6 +486,46 @@ int cg_lexbfs_order_dense(cg_context *ctx, const cg_dense *g, int32_t *order, in
     return run_single_dense(ctx, g, order, pos, nullptr, nullptr, stream);
 }
 
+int cg_lexbfs_sweep_dense(cg_context *ctx, const cg_dense *g, int32_t kind, const int32_t *tiebreak, int32_t start,
+                          int32_t *order, int32_t *pos, cudaStream_t stream) {
+    int rc;
+    if ((rc = check_ctx(ctx)) || (rc = check_dense(g))) return rc;
+    const int n = g->n;
+    if (n > 0 && !order) return set_error(CG_EINVAL, "null order pointer");
+    if (kind != CG_TIE_ID && kind != CG_TIE_RANK && kind != CG_TIE_LAST_IN)
+        return set_error(CG_EINVAL, "unknown tie-break kind %d", kind);
+    if (kind != CG_TIE_ID && n > 0 && !tiebreak) return set_error(CG_EINVAL, "null tie-break array");
+    if (start < -1 || (start >= 0 && start >= n)) return set_error(CG_EINVAL, "start %d outside [-1, n)", start);
+    if (kind == CG_TIE_ID && start < 0) return run_single_dense(ctx, g, order, pos, nullptr, nullptr, stream);
+    if (n == 0) return CG_OK;
+    LexPlan plan;
+    if ((rc = lexbfs_dense_plan(n, ctx->cfg.threads_override, &plan))) return rc;
+    const size_t wn = (size_t)(n + 31) / 32;
+    Carve cv;
+    const size_t o_prow = cv.take<uint32_t>((size_t)n * wn);
+    const size_t o_rank = cv.take<int32_t>(n), o_newid = cv.take<int32_t>(n), o_inv = cv.take<int32_t>(n);
+    const size_t o_seen = cv.take<int>(n), o_order = cv.take<int32_t>(n), o_pos = cv.take<int32_t>(n);
+    const size_t o_flag = cv.take<int>(1), o_counter = cv.take<int>(1);
+    const size_t o_gstate = cv.take<unsigned char>(plan.gstate_bytes);
+    if ((rc = ensure_ws(ctx, cv.off))) return rc;
+    SweepBuffers sb{at<uint32_t>(ctx, o_prow), at<int32_t>(ctx, o_rank), at<int32_t>(ctx, o_newid),
+                    at<int32_t>(ctx, o_inv), at<int>(ctx, o_seen), at<int32_t>(ctx, o_order),
+                    at<int32_t>(ctx, o_pos), at<int>(ctx, o_flag)};
+    PhaseTimer pt(ctx, &ctx->ev_lex, stream);
+    if ((rc = sweep_ids_launch(n, kind, tiebreak, start, sb, ctx->num_sms, stream))) return rc;
+    if (ctx->cfg.validate) {   // before the search runs on the relabelled copy
+        int flag = 0;
+        CG_CUDA_TRY(cudaMemcpyAsync(&flag, sb.flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CG_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (flag) return set_error(CG_EINVAL, "tie-break array is not a permutation of 0..n-1");
+    }
+    rc = sweep_order_launch(desc_of(g, 0, 0), plan, plan.gstate_bytes ? at<void>(ctx, o_gstate) : nullptr,
+                            at<int>(ctx, o_counter), sb, order, pos, ctx->num_sms, stream);
+    if (rc) return rc;
+    ctx->launches += 5;
+    return CG_OK;
+}
+
 int cg_chordal_test_dense(cg_context *ctx, const cg_dense *g, cg_result *res, int32_t *order, cudaStream_t stream) {
     int rc;
     if ((rc = check_ctx(ctx)) || (rc = check_dense(g))) return rc;

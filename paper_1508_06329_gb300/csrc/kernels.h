@@ -59,6 +59,24 @@ int fused_dense_launch(const FusedPlan &plan, const DenseDesc *descs, int count,
                        int32_t *pos, int32_t *parent, cg_result *res, int *work_counter, cudaStream_t stream);
 int fused_ctas_per_sm(const FusedPlan &plan);
 
+// ---- one multi-sweep LexBFS sweep on a dense graph (sweep_dense.cu)
+struct SweepBuffers {
+    uint32_t *prow;     // relabelled matrix, n * ceil(n/32) words
+    int32_t *rankv;     // n each below
+    int32_t *newid;
+    int32_t *inv;
+    int *seen;
+    int32_t *order_p;
+    int32_t *pos_p;
+    int *flag;          // 1 int: set when the tie-break array is not a permutation
+};
+// new ids from the tie-break array (sets *sb.flag if it is not a permutation)
+int sweep_ids_launch(int n, int kind, const int32_t *tiebreak, int start, const SweepBuffers &sb, int num_sms,
+                     cudaStream_t stream);
+// relabelled matrix, LexBFS on it, order / pos mapped back
+int sweep_order_launch(const DenseDesc &d, const LexPlan &plan, void *gstate, int *counter, const SweepBuffers &sb,
+                       int32_t *order, int32_t *pos, int num_sms, cudaStream_t stream);
+
 // ---- dense MCS (mcs_dense.cu): one CTA per graph, n <= 65520
 int mcs_dense_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, int ctas, int32_t *order,
                      int32_t *pos, int *work_counter, cudaStream_t stream);

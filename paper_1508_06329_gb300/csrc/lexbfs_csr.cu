@@ -24,7 +24,7 @@
 //     member, open run) stamped with the step number, in four passes; rows of
 //     at most 32 neighbours take a register-only single pass.
 // parent[y] = x is recorded for every moved y: the last pivot that moves y is
-// p(y) of the perfect-elimination check (Section 5.3).
+// p(y) of the perfect-elimination check (Section 5.2).
 #include <algorithm>
 
 #include "kernels.h"

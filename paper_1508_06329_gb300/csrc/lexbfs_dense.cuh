@@ -3,7 +3,7 @@
 // Method (Section 4.2 of the paper; its GPU form in Section 6.1): the
 // unnumbered vertices are partitioned into classes ordered top first.  Each
 // step visits the first vertex x of the first class, then replaces every
-// class C by C ∩ N_x followed by C \ N_x (Observation 6.1: the new class goes
+// class C by C ∩ N_x followed by C \ N_x (Observation 6.2: the new class goes
 // right before the class it came from).  Within a class vertices are kept in
 // id order, so the visited vertex is the lowest id of the top class.
 //
@@ -33,7 +33,7 @@
 //     first (lowest) candidate of the top class to the pivot atomicMin;
 //   * every moved vertex y records parent[y] = x; the last pivot that moves y
 //     is its neighbour with the largest order index below its own, i.e.
-//     p(y) of the perfect-elimination check (Section 5.3), so the check does
+//     p(y) of the perfect-elimination check (Section 5.2), so the check does
 //     not rescan rows to find parents;
 //   * the graph's rows are bulk-prefetched into L2 when the CTA starts.
 #pragma once

@@ -1,6 +1,6 @@
 // mcs_dense.cu — Maximum Cardinality Search on dense graphs, one CTA per graph.
 //
-// Method (Section 5.2; Tarjan and Yannakakis): every unnumbered vertex carries
+// Method (Section 5.1; Tarjan and Yannakakis): every unnumbered vertex carries
 // the number of its numbered neighbours; each step numbers a vertex with the
 // largest count (lowest id among equals, as for LexBFS) and counts it at its
 // unnumbered neighbours.  By Theorem 5.2 the graph is chordal iff the MCS

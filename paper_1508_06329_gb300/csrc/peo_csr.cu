@@ -1,4 +1,4 @@
-// peo_csr.cu — perfect-elimination check of CSR graphs (Sections 5.3, 6.2).
+// peo_csr.cu — perfect-elimination check of CSR graphs (Sections 5.2, 6.2).
 //
 // One warp per vertex v: p = p(v) (recorded by the CSR LexBFS, or computed
 // here for a caller's order as the neighbour with the largest order index

@@ -1,4 +1,4 @@
-// peo_dense.cu — perfect-elimination check of dense graphs (Sections 5.3, 6.2).
+// peo_dense.cu — perfect-elimination check of dense graphs (Sections 5.2, 6.2).
 //
 // For every vertex v (one warp per vertex, all graphs of a batch in one grid):
 //   p(v)  = the neighbour of v with the largest order index below pos(v)

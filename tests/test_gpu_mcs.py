@@ -1,4 +1,4 @@
-"""GPU parity of the MCS ordering (Section 5.2) and the test built on it
+"""GPU parity of the MCS ordering (Section 5.1) and the test built on it
 (Theorem 5.2) against the CPU oracle: order and witness bit-exact."""
 import numpy as np
 import pytest

@@ -9,7 +9,7 @@ fix, never against the oracle itself.
   class-splitting form (Section 4.2) give the identical order; property LB
   holds for every triple (Lemma 4.2);
 * witness: the certificate (u, p in LN(v), p rightmost, u not adjacent to p),
-  v is the first vertex whose left neighbourhood is not a clique (Section 5.4),
+  v is the first vertex whose left neighbourhood is not a clique (Section 5.3),
   u is the smallest id of the violating set;
 * hand-derived small cases.
 """
@@ -268,7 +268,7 @@ def test_parent_array_by_definition():
 
 
 def test_peo_check_of_arbitrary_order():
-    """The check itself (Section 5.3) on orders that are not LexBFS orders: its
+    """The check itself (Section 5.2) on orders that are not LexBFS orders: its
     verdict equals the definition of a perfect elimination order."""
     rs = gg.rng_stream(555, 100)
     for t in range(50):
@@ -318,7 +318,7 @@ def test_planted_cycle_and_closing_edges_not_chordal():
         assert len(pairs) == 1 + s and oracle.chordal_test(h2).chordal == 0
 
 
-# ----------------------------------------------------------------- MCS (Section 5.2)
+# ----------------------------------------------------------------- MCS (Section 5.1)
 
 @pytest.mark.parametrize("n,p", [(10, 0.3), (60, 0.1), (150, 0.05), (200, 0.4)])
 def test_mcs_order_equals_definition(n, p):
