@@ -20,6 +20,9 @@ Other workloads (same JSON line; not run by default):
              density U[0.01, 0.2], dense below N = 8,192, CSR above; arrival
              rate 0.8 x the measured saturation throughput; p50 / p99 latency
 
+`--workload sweep16k` times one multi-sweep LexBFS sweep (LexBFS+ of the
+plain LexBFS order) on each graph of the N=16,384 pair; unit sweeps/s.
+
 `--order mcs` (dense16k, small1k) runs the same test with the Maximum
 Cardinality Search order (Section 5.1) instead of LexBFS: one graph per call,
 the two graphs on two streams.
@@ -145,6 +148,12 @@ def make_workload(name: str):
                                                                               info["r"]),
                         "n": g.n, "words_per_row": g.words, "graphs_per_step": 2,
                         "edges": [g.num_edges(), h.num_edges()], "bytes_per_graph": g.nbytes}
+    if name == "sweep16k":
+        g, h, info = gg.large_dense_pair()
+        return [g, h], {"workload": "one LexBFS+ sweep (multi-sweep LexBFS) of each graph of the dense N=16384 pair "
+                                    "(subtree-intersection chordal graph, density %.3f, + %d cycle-closing edges); "
+                                    "previous sweep = the plain LexBFS order" % (g.density(), info["r"]),
+                        "n": g.n, "words_per_row": g.words, "graphs_per_step": 2}
     if name == "small1k":
         g, h, info = gg.small_dense_pair()
         return [g, h], {"workload": "dense N=1000 subtree-intersection chordal graph (500-node tree) + copy with a "
@@ -253,6 +262,12 @@ def run_reference(args):
     if args.order == "mcs":
         cfg = dict(cfg, order="MCS (Section 5.1)")
     test = oracle_test_fn(args.order)
+    if args.workload == "sweep16k":
+        import oracle
+        prev = {id(g): oracle.lexbfs(g) for g in graphs}
+
+        def test(g):
+            return oracle.lexbfs_plus(g, prev[id(g)])
     sample = graphs if args.workload != "batch4096" else graphs[:512]
     for _ in range(args.warmup):
         test(sample[0])
@@ -264,14 +279,16 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = len(sample) * args.steps / total
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    unit = UNIT if args.workload != "sweep16k" else "sweeps/s"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 bitsets / int32",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT if args.workload != "sweep16k" else "sweeps/s", "cores": 1,
+                             "kind": "oracle",
                              "sample": f"{args.steps} steps x {len(sample)} graphs of the workload, "
                                        "single-threaded C oracle"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
@@ -473,6 +490,143 @@ def run_paper7(args):
             "table": table}
     print(json.dumps(line))
     ctx.close()
+    return 0
+
+
+def run_sweep(args):
+    """One LexBFS+ sweep per graph of the N=16,384 pair (two streams), each
+    fed the plain LexBFS order as the previous sweep; the sweep relabels the
+    graph on the GPU and runs the dense LexBFS on the copy."""
+    import numpy as np
+    import torch
+    import oracle
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1508_06329_gb300 import build as cbuild
+    cbuild.build()
+    from paper_1508_06329_gb300 import binding as B
+    graphs, cfg = make_workload("sweep16k")
+    prev_h = [oracle.lexbfs(g) for g in graphs]
+    want = [oracle.lexbfs_plus(g, p) for g, p in zip(graphs, prev_h)]
+    rows = [torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).to(dev) for g in graphs]
+    prev = [torch.from_numpy(p.astype(np.int32)).to(dev) for p in prev_h]
+    orders = [torch.empty(g.n, dtype=torch.int32, device=dev) for g in graphs]
+    stream = torch.cuda.current_stream()
+    side = [torch.cuda.Stream(dev) for _ in graphs]
+    ctxs = [B.Context(local) for _ in graphs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(plain=False):
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        for k, g in enumerate(graphs):
+            side[k].wait_event(ev)
+            if plain:
+                B.lexbfs_order_dense(ctxs[k], rows[k], g.n, orders[k], None, side[k])
+            else:
+                B.lexbfs_plus_dense(ctxs[k], rows[k], g.n, prev[k], orders[k], None, stream=side[k])
+        for s_ in side:
+            stream.wait_stream(s_)
+
+    def timed(plain, steps):
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(plain)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms
+
+    warm = max(args.warmup, 3)
+    timed(False, warm)
+    for k in range(len(graphs)):
+        if not np.array_equal(orders[k].cpu().numpy(), want[k]):
+            raise SystemExit("parity failure in the sweep bench")
+    for c in ctxs:
+        c.read_profile()
+        c.profile(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms = timed(False, args.steps)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    prof = {}
+    for c in ctxs:
+        for k, v in c.read_profile().items():
+            prof[k] = prof.get(k, 0) + v
+        c.profile(False)
+    total_ms, value = aggregate_over_ranks(sum(ms), len(graphs) * args.steps, dev)
+    plain_ms = timed(True, max(3, min(args.steps, 5)))
+    # end to end: previous order and rows from pinned host memory, the new order back
+    host_rows = [torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).pin_memory() for g in graphs]
+    host_prev = [p.cpu().pin_memory() for p in prev]
+    host_out = [torch.empty(g.n, dtype=torch.int32).pin_memory() for g in graphs]
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for hr, dr, hp, dp in zip(host_rows, rows, host_prev, prev):
+            dr.copy_(hr, non_blocking=True)
+            dp.copy_(hp, non_blocking=True)
+        step()
+        for ho, o in zip(host_out, orders):
+            ho.copy_(o, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if rank == 0 and any(not np.array_equal(ho.numpy(), w) for ho, w in zip(host_out, want)):
+        raise SystemExit("parity failure on the host-buffer path")
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    n, words = graphs[0].n, graphs[0].words
+    sweep_ms = prof["lexbfs_ms"] / max(1, prof["lexbfs_launches"])
+    lex_bytes = n * words * 4
+    line = {
+        "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps, "warmup": warm,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 bitsets / int32 (exact)", "data": "synthetic",
+        "config": dict(cfg, l2="flushed before each timed step (256 MiB write)",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "roofline": {"bound": "hbm", "kernel": "lexbfs_dense_kernel on the relabelled copy", "achieved":
+                     lex_bytes / (sweep_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": lex_bytes / (sweep_ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                     "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": lex_bytes},
+        "phases": {"sweep_ms_per_graph": sweep_ms, "step_ms_p50": statistics.median(ms),
+                   "plain_lexbfs_step_ms_p50": statistics.median(plain_ms),
+                   "relabel_overhead_ms_per_step": statistics.median(ms) - statistics.median(plain_ms)},
+        "e2e": {"value": len(graphs) * e2e_steps * world / e2e_s, "unit": "sweeps/s",
+                "h2d_bytes_per_step": sum(g.nbytes + 4 * g.n for g in graphs),
+                "d2h_bytes_per_step": sum(4 * g.n for g in graphs),
+                "path": "pinned host rows + previous order -> device, cg_lexbfs_sweep_dense (LexBFS+), order -> host"},
+        "gpu_launches": int(prof["kernel_launches"]),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1:
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < 10.0:
+            for g, p in zip(graphs, prev_h):
+                oracle.lexbfs_plus(g, p)
+                done += 1
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / el, "unit": "sweeps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{done} LexBFS+ sweeps of the two graphs, {el:.1f} s, single-threaded C"}
+    if rank == 0:
+        print(json.dumps(line))
+    for c in ctxs:
+        c.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -739,7 +893,8 @@ def main():
     ap.add_argument("--order", default="lexbfs", choices=["lexbfs", "mcs"],
                     help="vertex ordering of the test (dense workloads): LexBFS (default) or MCS")
     ap.add_argument("--workload", default="dense16k",
-                    choices=["dense16k", "small1k", "sparse1m", "sparse64k", "batch4096", "serve", "paper7"])
+                    choices=["dense16k", "small1k", "sparse1m", "sparse64k", "batch4096", "serve", "paper7",
+                             "sweep16k"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -747,6 +902,8 @@ def main():
         return run_serve(args)
     if args.workload == "paper7":
         return run_paper7(args)
+    if args.workload == "sweep16k":
+        return run_sweep(args)
     return run_gpu(args)
 
 
