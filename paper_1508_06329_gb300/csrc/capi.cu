@@ -185,12 +185,18 @@ int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const in
         packed += graphs[k].n;
     }
     for (int b = 0; b < kBuckets; ++b) L->bk[b] = BatchLayout::Bucket{};
+    int64_t eoff = 0;
     for (int j = 0; j < count; ++j) {
         const int k = idx[j];
         L->voff[j] = total;
         L->descs[j] = desc_of(&graphs[k], total, obase[k], k);
+        if (bucket[k] == 9) {   // graphs checked by the grid-wide kernel get earlier-than masks
+            L->descs[j].ebase = eoff;
+            eoff += earlier_mask_words(graphs[k].n);
+        }
         total += graphs[k].n;
     }
+    L->emask_words = eoff;
     L->voff[count] = total;
     L->total = total;
     int j = 0;
@@ -230,6 +236,7 @@ BatchBuffers batch_buffers(const BatchLayout &L, bool need_order) {
     bb.o_counter = cv.take<int>(kBuckets * 64);
     const auto &B9 = L.bk[9];
     bb.o_gstate = cv.take<unsigned char>(B9.end > B9.begin ? B9.lplan.gstate_bytes * B9.ctas : 0);
+    bb.o_emask = cv.take<uint32_t>(L.emask_words);
     bb.bytes = cv.off;
     return bb;
 }
@@ -266,18 +273,20 @@ int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
         } else {
             {
                 PhaseTimer pt(tctx, &ctx->ev_lex, s);
-                if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, nullptr,
-                                              B.lplan.gstate_bytes ? P(bb.o_gstate) : nullptr, counters + 64 * b, s)))
+                if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, parent,
+                                              B.lplan.gstate_bytes ? P(bb.o_gstate) : nullptr, counters + 64 * b, s,
+                                              1)))
                     return rc;
             }
             PhaseTimer pt(tctx, &ctx->ev_check, s);
             // the check over this bucket's vertices (a slice of the offset table)
             if ((rc = peo_dense_launch(ddesc + B.begin, DenseDesc{}, cnt, dvoff + B.begin, B.vend - B.vbegin, order,
-                                       pos, parent, false, keys + B.begin, ctx->num_sms, s)))
+                                       pos, parent, false, keys + B.begin, ctx->num_sms, s,
+                                       reinterpret_cast<uint32_t *>(P(bb.o_emask)), B.nmax, true)))
                 return rc;
             if ((rc = finalize_launch(ddesc + B.begin, DenseDesc{}, cnt, keys + B.begin, order, parent, res, s)))
                 return rc;
-            if (account) ctx->launches += 3;
+            if (account) ctx->launches += 4;
         }
         CG_CUDA_TRY(cudaEventRecord(ss.join[b], s));
         CG_CUDA_TRY(cudaStreamWaitEvent(stream, ss.join[b], 0));
@@ -311,6 +320,21 @@ int upload_layout(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
     return CG_OK;
 }
 
+// Workspace layout of run_single_dense (also the start of the host entry's).
+struct SingleDenseCarve {
+    size_t o_order, o_pos, o_parent, o_key, o_counter, o_gstate, o_emask;
+    Carve cv;
+    SingleDenseCarve(int n, const LexPlan &plan) {
+        o_order = cv.take<int32_t>(n);
+        o_pos = cv.take<int32_t>(n);
+        o_parent = cv.take<int32_t>(n);
+        o_key = cv.take<unsigned long long>(1);
+        o_counter = cv.take<int>(1);
+        o_gstate = cv.take<unsigned char>(plan.gstate_bytes);
+        o_emask = cv.take<uint32_t>(earlier_mask_words(n));
+    }
+};
+
 // LexBFS and (optionally) the check for one graph given by value.
 int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int32_t *pos_out, cg_result *res,
                      int32_t *parent_out, cudaStream_t stream) {
@@ -318,33 +342,31 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
     LexPlan plan;
     int rc = lexbfs_dense_plan(n, ctx->cfg.threads_override, &plan);
     if (rc) return rc;
-    Carve cv;
-    const size_t o_order = cv.take<int32_t>(n);
-    const size_t o_pos = cv.take<int32_t>(n);
-    const size_t o_parent = cv.take<int32_t>(n);
-    const size_t o_key = cv.take<unsigned long long>(1);
-    const size_t o_counter = cv.take<int>(1);
-    const size_t o_gstate = cv.take<unsigned char>(plan.gstate_bytes);
-    if ((rc = ensure_ws(ctx, cv.off))) return rc;
+    const SingleDenseCarve sc(n, plan);
+    const size_t o_order = sc.o_order, o_pos = sc.o_pos, o_parent = sc.o_parent, o_key = sc.o_key;
+    const size_t o_counter = sc.o_counter, o_gstate = sc.o_gstate, o_emask = sc.o_emask;
+    if ((rc = ensure_ws(ctx, sc.cv.off))) return rc;
     int32_t *order = order_out ? order_out : at<int32_t>(ctx, o_order);
     int32_t *pos = pos_out ? pos_out : at<int32_t>(ctx, o_pos);
     int32_t *parent = parent_out ? parent_out : at<int32_t>(ctx, o_parent);
     const DenseDesc d = desc_of(g, 0, 0);
     if (n > 0) {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
-        // parents are recomputed by the check: per-step parent stores in the
-        // search cost more than the check's rescan (measured on N = 16,384)
-        rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, nullptr,
-                                 plan.gstate_bytes ? at<void>(ctx, o_gstate) : nullptr, at<int>(ctx, o_counter), stream);
+        // the search records the parents of pivots that neighbour the previous
+        // pivot (one store per step); the check finds the rest
+        rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, res ? parent : nullptr,
+                                 plan.gstate_bytes ? at<void>(ctx, o_gstate) : nullptr, at<int>(ctx, o_counter), stream,
+                                 1);
         if (rc) return rc;
         ctx->launches += 1;
     }
     if (!res) return CG_OK;
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
     unsigned long long *key = at<unsigned long long>(ctx, o_key);
-    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream)))
+    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream,
+                               at<uint32_t>(ctx, o_emask), n, true)))
         return rc;
-    ctx->launches += n > 0 ? 2 : 1;
+    ctx->launches += n > 0 ? 3 : 1;
     return finalize_launch(nullptr, d, 1, key, order, parent, res, stream);
 }
 
@@ -544,16 +566,28 @@ int cg_peo_check_dense(cg_context *ctx, const cg_dense *g, const int32_t *order,
     const size_t o_pos = cv.take<int32_t>(n);
     const size_t o_parent = cv.take<int32_t>(n);
     const size_t o_key = cv.take<unsigned long long>(1);
+    const size_t o_emask = cv.take<uint32_t>(earlier_mask_words(n));
+    const size_t o_flag = cv.take<int>(1);
     if ((rc = ensure_ws(ctx, cv.off))) return rc;
     int32_t *pos = at<int32_t>(ctx, o_pos);
     int32_t *par = parent ? parent : at<int32_t>(ctx, o_parent);
     unsigned long long *key = at<unsigned long long>(ctx, o_key);
     const DenseDesc d = desc_of(g, 0, 0);
+    if (ctx->cfg.validate) {   // the position buffer doubles as the seen flags
+        if ((rc = order_check_launch(n, order, pos, at<int>(ctx, o_flag), ctx->num_sms, stream))) return rc;
+        int flag = 0;
+        CG_CUDA_TRY(cudaMemcpyAsync(&flag, at<int>(ctx, o_flag), sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CG_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (flag) return set_error(CG_EINVAL, "order is not a permutation of 0..n-1");
+    }
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
+    // vertices missing from an invalid order keep position -1 and are skipped
+    if (n > 0) CG_CUDA_TRY(cudaMemsetAsync(pos, 0xFF, sizeof(int32_t) * (size_t)n, stream));
     if ((rc = invert_order_launch(nullptr, d, 1, nullptr, n, order, pos, ctx->num_sms, stream))) return rc;
-    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, par, false, key, ctx->num_sms, stream)))
+    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, par, false, key, ctx->num_sms, stream,
+                               at<uint32_t>(ctx, o_emask), n)))
         return rc;
-    ctx->launches += n > 0 ? 3 : 1;
+    ctx->launches += n > 0 ? 4 : 1;
     return finalize_launch(nullptr, d, 1, key, order, par, res, stream);
 }
 
@@ -567,13 +601,7 @@ int cg_chordal_test_dense_host(cg_context *ctx, int32_t n, int32_t words_per_row
     LexPlan plan;
     if ((rc = lexbfs_dense_plan(n, ctx->cfg.threads_override, &plan))) return rc;
     // device copies of the inputs and outputs live past the scratch used by run_single_dense
-    Carve cv;
-    cv.take<int32_t>(n);
-    cv.take<int32_t>(n);
-    cv.take<int32_t>(n);
-    cv.take<unsigned long long>(1);
-    cv.take<int>(1);
-    cv.take<unsigned char>(plan.gstate_bytes);
+    Carve cv = SingleDenseCarve(n, plan).cv;
     const size_t bytes_rows = (size_t)n * words_per_row * sizeof(uint32_t);
     const size_t o_rows = cv.take<unsigned char>(bytes_rows);
     const size_t o_res = cv.take<cg_result>(1);
@@ -603,6 +631,7 @@ int run_mcs_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int32_
     const size_t o_parent = cv.take<int32_t>(n);
     const size_t o_key = cv.take<unsigned long long>(1);
     const size_t o_counter = cv.take<int>(1);
+    const size_t o_emask = cv.take<uint32_t>(res ? earlier_mask_words(n) : 0);
     int rc;
     if ((rc = ensure_ws(ctx, cv.off))) return rc;
     int32_t *order = order_out ? order_out : at<int32_t>(ctx, o_order);
@@ -617,9 +646,10 @@ int run_mcs_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int32_
     if (!res) return CG_OK;
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
     unsigned long long *key = at<unsigned long long>(ctx, o_key);
-    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream)))
+    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream,
+                               at<uint32_t>(ctx, o_emask), n)))
         return rc;
-    ctx->launches += n > 0 ? 2 : 1;
+    ctx->launches += n > 0 ? 3 : 1;
     return finalize_launch(nullptr, d, 1, key, order, parent, res, stream);
 }
 }  // namespace

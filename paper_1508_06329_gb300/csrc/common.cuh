@@ -49,6 +49,9 @@ __device__ __forceinline__ void prefetch_range_l2(const void *base, size_t bytes
     }
 }
 
+// Parent value meaning "not known yet": the dense check finds it.
+constexpr int kParentUnresolved = -2;
+
 // Per-graph descriptor as the kernels see it (device memory).
 struct DenseDesc {
     const uint32_t *rows;   // n * words
@@ -58,6 +61,7 @@ struct DenseDesc {
     int64_t obase;          // offset of this graph's order in the caller's order array
     int32_t rindex;         // slot of this graph's result
     int32_t pad;
+    int64_t ebase;          // word offset of this graph's earlier-than masks in the check's mask buffer
 };
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

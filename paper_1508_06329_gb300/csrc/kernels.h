@@ -26,17 +26,28 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan);
 // descs: device array, or nullptr to use `single` (count must be 1).
 // work_counter: device int, zeroed by the launcher (dynamic graph hand-out).
 // parent (nullable) receives p(v) for every vertex, recorded during the search.
+// parent (packed by vbase) receives parents when non-null: parent_mode 0
+// records p(v) for every vertex (a store per moved vertex), 1 only for the
+// pivots chosen among the moved vertices (kParentUnresolved for the others).
 int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                         int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
-                        cudaStream_t stream);
+                        cudaStream_t stream, int parent_mode = 0);
 
 // ---- dense perfect-elimination check (peo_dense.cu)
 // keys: device u64[count], set to ~0 by the launcher.
 // parent_known: parent[] already holds p(v) (from the search); otherwise the
 // kernel computes it from the rows and writes it.
+// emask: workspace for the graphs' earlier-than masks (earlier_mask_words(n)
+// words at each desc's ebase; n_max = the largest n), or null for the
+// gather-based check.  prefilled (with masks, parent_known false): parent
+// already holds p(v) or kParentUnresolved for each v (from the search).
 int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
                      const int32_t *order, const int32_t *pos, int32_t *parent, bool parent_known,
-                     unsigned long long *keys, int num_sms, cudaStream_t stream);
+                     unsigned long long *keys, int num_sms, cudaStream_t stream, uint32_t *emask = nullptr,
+                     int n_max = 0, bool prefilled = false);
+int64_t earlier_mask_words(int n);
+// sets *flag when order is not a permutation of 0..n-1 (seen: n ints of scratch)
+int order_check_launch(int n, const int32_t *order, int *seen, int *flag, int num_sms, cudaStream_t stream);
 
 // pos[order[i]] = i for every graph (order values outside 0..n-1 are skipped).
 int invert_order_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,

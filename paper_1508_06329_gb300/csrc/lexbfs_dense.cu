@@ -17,7 +17,7 @@ template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, bool SPLIT = fal
 __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
                                                          int count, int32_t *__restrict__ order,
                                                          int32_t *__restrict__ pos, int32_t *__restrict__ parent,
-                                                         unsigned char *gstate, size_t gstate_stride,
+                                                         int pmode, unsigned char *gstate, size_t gstate_stride,
                                                          int *work_counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     LexScalars *sc = reinterpret_cast<LexScalars *>(smem);
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
             __syncthreads();
         }
         lexbfs_cta<Id, T, WPT, LPW>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr,
-                               parent ? parent + d.vbase : nullptr);
+                                    parent ? parent + d.vbase : nullptr, pmode);
         __syncthreads();
         if (count == 1) break;
     }
@@ -65,12 +65,12 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
 
 template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, bool SPLIT = false>
 int launch_variant(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
-                   int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
-                   cudaStream_t stream) {
+                   int32_t *order, int32_t *pos, int32_t *parent, int pmode, void *gstate,
+                   int *work_counter, cudaStream_t stream) {
     auto kern = lexbfs_dense_kernel<Id, T, WPT, LPW, ROWS_SMEM, SPLIT>;
     CG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes));
     if (count > 1) CG_CUDA_TRY(cudaMemsetAsync(work_counter, 0, sizeof(int), stream));
-    kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, single, count, order, pos, parent,
+    kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, single, count, order, pos, parent, pmode,
                                                static_cast<unsigned char *>(gstate), plan.gstate_bytes,
                                                work_counter);
     CG_LAUNCH_CHECK("lexbfs_dense_kernel");
@@ -120,27 +120,26 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
 
 int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                         int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, int parent_mode) {
     if (count <= 0) return CG_OK;
     ctas = std::max(1, std::min(ctas, count));
-    if (plan.split_state)
-        return launch_variant<uint16_t, 1024, 2, 1, false, true>(plan, descs, single, count, ctas, order, pos, parent,
-                                                                  gstate, work_counter, stream);
-    if (plan.wide_ids)
-        return launch_variant<uint32_t, 1024, 4, 1, false>(plan, descs, single, count, ctas, order, pos, parent, gstate,
-                                                         work_counter, stream);
+    auto go = [&](auto launch, void *gs) {
+        return launch(plan, descs, single, count, ctas, order, pos, parent, parent_mode, gs, work_counter, stream);
+    };
+    if (plan.split_state) return go(launch_variant<uint16_t, 1024, 2, 1, false, true>, gstate);
+    if (plan.wide_ids) return go(launch_variant<uint32_t, 1024, 4, 1, false>, gstate);
     switch (plan.threads) {
         case 128:
-            return plan.rows_smem ? launch_variant<uint16_t, 128, 4, 1, true>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream)
-                                  : launch_variant<uint16_t, 128, 4, 1, false>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream);
+            return plan.rows_smem ? go(launch_variant<uint16_t, 128, 4, 1, true>, nullptr)
+                                  : go(launch_variant<uint16_t, 128, 4, 1, false>, nullptr);
         case 256:
-            return plan.rows_smem ? launch_variant<uint16_t, 256, 2, 1, true>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream)
-                                  : launch_variant<uint16_t, 256, 2, 1, false>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream);
+            return plan.rows_smem ? go(launch_variant<uint16_t, 256, 2, 1, true>, nullptr)
+                                  : go(launch_variant<uint16_t, 256, 2, 1, false>, nullptr);
         case 512:
-            return plan.rows_smem ? launch_variant<uint16_t, 512, 1, 1, true>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream)
-                                  : launch_variant<uint16_t, 512, 1, 1, false>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream);
+            return plan.rows_smem ? go(launch_variant<uint16_t, 512, 1, 1, true>, nullptr)
+                                  : go(launch_variant<uint16_t, 512, 1, 1, false>, nullptr);
         default:
-            return launch_variant<uint16_t, 1024, 1, 2, false>(plan, descs, single, count, ctas, order, pos, parent, nullptr, work_counter, stream);
+            return go(launch_variant<uint16_t, 1024, 1, 2, false>, nullptr);
     }
 }
 

@@ -31,10 +31,13 @@
 //     unnumbered neighbours are visited; the deferred relabel and the split
 //     are two short loops over a word's bits, and a thread posts only its
 //     first (lowest) candidate of the top class to the pivot atomicMin;
-//   * every moved vertex y records parent[y] = x; the last pivot that moves y
-//     is its neighbour with the largest order index below its own, i.e.
-//     p(y) of the perfect-elimination check (Section 5.2), so the check does
-//     not rescan rows to find parents;
+//   * parents: p(y) of the perfect-elimination check (Section 5.2), y's
+//     neighbour with the largest order index below its own, is the last pivot
+//     that moved y.  kParentMoves stores it for every moved vertex (one store
+//     per edge; the one-CTA fused test wants all parents).  kParentPivots
+//     stores one value per step: a pivot chosen among the moved vertices has
+//     the current pivot as parent, one chosen by a class scan gets
+//     kParentUnresolved and the check finds its parent;
 //   * the graph's rows are bulk-prefetched into L2 when the CTA starts.
 #pragma once
 #include "common.cuh"
@@ -76,6 +79,10 @@ struct LexScalars {
 };
 
 constexpr unsigned kNoVertex = 0xFFFFFFFFu;
+
+// How lexbfs_cta records parents (when given a parent array).
+constexpr int kParentMoves = 0;        // every moved vertex: parent[y] = pivot
+constexpr int kParentPivots = 1;       // once per pivot: previous pivot, or kParentUnresolved
 
 template <typename Id>
 __host__ __device__ inline size_t lex_state_bytes(int n) {
@@ -147,13 +154,14 @@ __device__ __forceinline__ uint32_t row_word(const uint32_t *__restrict__ rows, 
 // One CTA computes the LexBFS order of one graph.  rows/stride address the
 // adjacency (global memory, or a compact shared-memory copy).  parent may be
 // null; otherwise parent[v] receives p(v) (or -1 when v has no earlier
-// neighbour).  lpw >= LPW threads share each row word (thread t takes bit
-// slice t % lpw of word t / lpw + k * T / lpw), which shortens the serial bit
-// loop; lpw grows while T / lpw still covers the row.
+// neighbour, or kParentUnresolved under kParentPivots).  lpw >= LPW threads
+// share each row word (thread t takes bit slice t % lpw of word t / lpw +
+// k * T / lpw), which shortens the serial bit loop; lpw grows while T / lpw
+// still covers the row.
 template <typename Id, int T, int WPT, int LPW>
 __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n, LexState<Id> st,
                            LexScalars *sc, int32_t *__restrict__ order, int32_t *__restrict__ pos,
-                           int32_t *__restrict__ parent) {
+                           int32_t *__restrict__ parent, int pmode = kParentMoves) {
     using Tr = IdTraits<Id>;
     using Sz = typename Tr::Sz;
     const Id kNumbered = (Id)~(Id)0;
@@ -175,7 +183,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
 
     for (int v = t; v < n; v += T) {
         st.cls[v] = 0;
-        if (parent) parent[v] = -1;
+        if (parent && pmode == kParentMoves) parent[v] = -1;
     }
     for (int k = t; k < n - 1; k += T) st.freel[k] = (Id)(k + 1);
     for (int w = t; w < wn; w += T) st.numbered[w] = 0u;
@@ -199,6 +207,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
         amask[k] = 0u;
     }
     Id pending_free = kNone;
+    int par_x = -1;   // p(x) of the current pivot (thread 0, kParentPivots)
     __syncthreads();
 
     for (int i = 0; i < n; ++i) {
@@ -216,6 +225,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             }
             order[i] = x;
             if (pos) pos[x] = i;
+            if (parent && pmode == kParentPivots) parent[x] = par_x;
         }
 #pragma unroll
         for (int k = 0; k < WPT; ++k) {
@@ -251,7 +261,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                         atomicMin(&sc->second_min[slot], (unsigned)y);
                         g_done = true;
                     }
-                    if (parent) parent[y] = x;
+                    if (parent && pmode == kParentMoves) parent[y] = x;
                 }
                 if (w == (x >> 5) && ((part >> (x & 31)) & 1u)) {
                     st.cls[x] = kNumbered;
@@ -285,6 +295,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             mode = 2;
             target = g;
         }
+        if (t == 0) par_x = mode == 0 ? x : kParentUnresolved;   // a moved pivot's parent is x
         if (mode == 0) {
 #pragma unroll
             for (int k = 0; k < WPT; ++k) {

@@ -105,7 +105,7 @@ extern "C" int cg_chordal_test_dense_noalloc(const cg_dense *g, cg_result *res, 
     int32_t *ord = order ? order : reinterpret_cast<int32_t *>(scratch + kOffOrder);
     unsigned long long *key = reinterpret_cast<unsigned long long *>(scratch + kOffKey);
     int *counter = reinterpret_cast<int *>(scratch + kOffCounter);
-    DenseDesc d;
+    DenseDesc d{};
     d.rows = g->rows;
     d.n = n;
     d.words = g->words_per_row;

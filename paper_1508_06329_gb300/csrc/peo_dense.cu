@@ -1,16 +1,23 @@
 // peo_dense.cu — perfect-elimination check of dense graphs (Sections 5.2, 6.2).
 //
-// For every vertex v (one warp per vertex, all graphs of a batch in one grid):
+// For every vertex v (one warp per vertex, all graphs of a bucket in one grid):
 //   p(v)  = the neighbour of v with the largest order index below pos(v)
-//           (the paper's preparationLNandP kernel) — taken from the LexBFS
-//           kernel, which records it, or computed here for a given order;
+//           (the paper's preparationLNandP kernel);
 //   bad   = (LN_v - {p}) \ N(p), evaluated word by word as row_v & ~row_p and
 //           kept only for bits u != p with pos(u) < pos(v) (the paper's
-//           testing kernel, with p itself excluded);
-// and the first violation in order is found by an atomicMin over the 64-bit
-// key (pos(v) << 32 | u), u being the lowest id of bad(v) (the lane whose word
-// holds the lowest violating bit wins the warp min-reduction).
-// The finalize kernel turns each graph's key into (chordal, v, p, u).
+//           testing kernel, with p itself excluded).
+// GPU form: peo_prep_kernel builds "earlier-than" masks (E_b: the vertices
+// numbered before position 32 b, one bit row per group of 32 positions) and,
+// one thread per vertex, finds p(v) among the 32 positions before pos(v)
+// (where it lies for ~95% of the vertices of a LexBFS order); the check warp
+// then streams row v, row p(v) and E_b (restricting to earlier vertices is a
+// word-wise AND, no pos gathers) and finds the remaining parents by probing
+// groups of 32 positions and a binary search over the masks.  Without masks
+// (the fixed-scratch entry point) p(v) comes from the caller or from pos
+// gathers over row v.
+// The first violation in order is found by an atomicMin over the 64-bit
+// key (pos(v) << 32 | u), u being the lowest id of bad(v); the finalize
+// kernel turns each graph's key into (chordal, v, p, u).
 #include <algorithm>
 
 #include "kernels.h"
@@ -21,16 +28,58 @@ namespace {
 
 constexpr int kPeoThreads = 256;
 
-constexpr int kRC = 16;   // row words per lane held in registers (512 words = 16,384 vertices per chunk)
+constexpr int kRC = 8;    // row words per lane held in registers (256 words = 8,192 vertices per chunk)
 
+// "Earlier-than" masks: for each group b of 32 positions, E_b has bit u set
+// iff pos(u) < 32 b.  ceil(n/32)^2 words per graph at emask + ebase, row b = E_b.
+constexpr int kMaskRows = 32;         // rows b per mask tile
+constexpr int kScan = 32;             // positions a prep thread scans for p(v)
+
+// p(v) by gathering pos over every neighbour: max pos(u) < pos(v).
+__device__ __forceinline__ int parent_by_gather(const uint32_t *__restrict__ rv, int wn, uint32_t lastmask,
+                                                const int32_t *__restrict__ pos_g, int pv, int lane) {
+    int best = -1;
+    for (int w = lane; w < wn; w += 32) {
+        uint32_t bits = __ldg(rv + w);
+        if (w == wn - 1) bits &= lastmask;
+        while (bits) {
+            const int u = (w << 5) + (__ffs(bits) - 1);
+            bits &= bits - 1;
+            const int pu = __ldg(pos_g + u);
+            if (pu < pv && pu > best) best = pu;
+        }
+    }
+    return __reduce_max_sync(0xFFFFFFFFu, best);
+}
+
+// |row ∩ mask| over the whole row (warp-wide sum).
+__device__ __forceinline__ int count_in(const uint32_t *__restrict__ row, const uint32_t *__restrict__ mask, int wn,
+                                        int lane) {
+    int c = 0;
+    for (int w = lane; w < wn; w += 32) c += __popc(__ldg(row + w) & __ldg(mask + w));
+    return __reduce_add_sync(0xFFFFFFFFu, c);
+}
+
+__device__ __forceinline__ bool has_bit(const uint32_t *__restrict__ row, int u) {
+    return (__ldg(row + (u >> 5)) >> (u & 31)) & 1u;
+}
+
+// emask: the "earlier-than" masks (built by peo_prep_kernel), or null.  With
+// masks, LN_v = row_v & (E_b | {order[32b .. pos(v) - 1]}) for b = pos(v) / 32,
+// so the subset test streams row v, row p(v) and E_b with no pos gathers, and
+// p(v) is found by probing the order backwards from pos(v) in groups of 32
+// (after kProbe groups without a neighbour, a binary search over the masks
+// finds the last group that holds one).
 template <bool PARENT_KNOWN>
-__global__ void __launch_bounds__(kPeoThreads) peo_dense_kernel(const DenseDesc *__restrict__ descs,
+__global__ void __launch_bounds__(kPeoThreads, 4) peo_dense_kernel(const DenseDesc *__restrict__ descs,
                                                                 DenseDesc single, int count,
                                                                 const int64_t *__restrict__ voff, int64_t total,
                                                                 const int32_t *__restrict__ order,
                                                                 const int32_t *__restrict__ pos,
                                                                 int32_t *__restrict__ parent,
+                                                                const uint32_t *__restrict__ emask,
                                                                 unsigned long long *__restrict__ keys) {
+    constexpr int kProbe = 4;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -51,67 +100,200 @@ __global__ void __launch_bounds__(kPeoThreads) peo_dense_kernel(const DenseDesc 
         const int wn = (d.n + 31) >> 5;
         const uint32_t lastmask = (d.n & 31) ? ((1u << (d.n & 31)) - 1u) : 0xFFFFFFFFu;
         const int32_t *pos_g = pos + d.vbase;
+        const int32_t *ord_g = order + d.obase;
         const int pv = __ldg(pos_g + v);
+        if (pv < 0 || pv >= d.n) continue;   // not in the order (only for an invalid caller order)
         const uint32_t *rv = d.rows + (size_t)v * d.words;
+        const uint32_t *E = emask ? emask + d.ebase + (size_t)(pv >> 5) * wn : nullptr;
 
-        int p;
-        if (PARENT_KNOWN) {
-            p = __ldg(parent + d.vbase + v);
-        } else {
-            int best = -1;
-            for (int w0 = 0; w0 < wn; w0 += 32 * kRC) {
-                uint32_t a[kRC];
+        uint32_t ae[kRC];   // row_v & E_b of one chunk
+        auto load_ae = [&](int w0) {
 #pragma unroll
-                for (int k = 0; k < kRC; ++k) {
-                    const int w = w0 + k * 32 + lane;
-                    a[k] = w < wn ? __ldg(rv + w) : 0u;
-                    if (w == wn - 1) a[k] &= lastmask;
-                }
-#pragma unroll
-                for (int k = 0; k < kRC; ++k) {
-                    uint32_t bits = a[k];
-                    const int w = w0 + k * 32 + lane;
-                    while (bits) {
-                        const int u = (w << 5) + (__ffs(bits) - 1);
-                        bits &= bits - 1;
-                        const int pu = __ldg(pos_g + u);
-                        if (pu < pv && pu > best) best = pu;
-                    }
-                }
+            for (int k = 0; k < kRC; ++k) {
+                const int w = w0 + k * 32 + lane;
+                ae[k] = w < wn ? __ldg(rv + w) & (E ? __ldg(E + w) : 0xFFFFFFFFu) : 0u;
             }
-            best = __reduce_max_sync(0xFFFFFFFFu, best);
-            p = best >= 0 ? __ldg(order + d.obase + best) : -1;
-            if (lane == 0) parent[d.vbase + v] = p;
+        };
+        // the vertices at positions 32b .. pos(v) - 1 (not in E_b), one per lane
+        const int a0 = pv & ~31;
+        int ux = -1;
+        bool xin = false;   // ux is a neighbour of v
+        if (E && lane < pv - a0) {
+            ux = __ldg(ord_g + a0 + lane);
+            xin = (unsigned)ux < (unsigned)d.n && has_bit(rv, ux);
         }
-        if (p < 0) continue;
+        int p;
+        if (PARENT_KNOWN || E) {
+            // known, or found by peo_prep_kernel's scan of the last kScan positions
+            p = __ldg(parent + d.vbase + v);
+        }
+        if (!PARENT_KNOWN) {
+            if (E) {
+                if (p == kParentUnresolved) {   // warp-wide: groups of 32 positions, then the masks
+                    p = -1;
+                    int c = (pv >> 5) - 1;
+                    for (int r = 0; c >= 0 && r < kProbe; --c, ++r) {
+                        const int u = __ldg(ord_g + c * 32 + lane);   // c * 32 + 31 < pos(v)
+                        const unsigned hit = __ballot_sync(0xFFFFFFFFu, (unsigned)u < (unsigned)d.n && has_bit(rv, u));
+                        if (hit) {
+                            p = __shfl_sync(0xFFFFFFFFu, u, 31 - __clz(hit));
+                            break;
+                        }
+                    }
+                    if (p < 0 && c >= 0) {
+                        // groups 0..c remain: F(g) = |row_v ∩ E_g| is nondecreasing in g; the
+                        // parent's group is the last g <= c with F(g) < F(c + 1)
+                        const int total = count_in(rv, emask + d.ebase + (size_t)(c + 1) * wn, wn, lane);
+                        if (total > 0) {
+                            int lo = 0, hi = c + 1;   // F(lo) < total = F(hi)
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (count_in(rv, emask + d.ebase + (size_t)mid * wn, wn, lane) == total) hi = mid;
+                                else lo = mid;
+                            }
+                            const int u = __ldg(ord_g + lo * 32 + lane);
+                            const unsigned hit =
+                                __ballot_sync(0xFFFFFFFFu, (unsigned)u < (unsigned)d.n && has_bit(rv, u));
+                            if (hit) p = __shfl_sync(0xFFFFFFFFu, u, 31 - __clz(hit));
+                        }
+                    }
+                    if (lane == 0) parent[d.vbase + v] = p;
+                }
+            } else {
+                const int best = parent_by_gather(rv, wn, lastmask, pos_g, pv, lane);
+                p = best >= 0 ? __ldg(ord_g + best) : -1;
+                if (lane == 0) parent[d.vbase + v] = p;
+            }
+        }
+        if (p < 0 || p >= d.n) continue;
 
-        // LN_v - {p} ⊆ N(p): scan row_v & ~row_p for an earlier vertex other than p
+        // LN_v - {p} ⊆ N(p): the lowest id among earlier vertices of row_v & ~row_p other than p
         const uint32_t *rp = d.rows + (size_t)p * d.words;
-        unsigned umin = 0xFFFFFFFFu;
+        unsigned xmin = 0xFFFFFFFFu;   // among the vertices at positions 32b .. pos(v) - 1
+        if (E) {
+            const bool bad = xin && ux != p && !has_bit(rp, ux);
+            xmin = __reduce_min_sync(0xFFFFFFFFu, bad ? (unsigned)ux : 0xFFFFFFFFu);
+        }
+        unsigned umin = 0xFFFFFFFFu;   // among the rest (E_b, or by pos gathers without masks)
         for (int w0 = 0; w0 < wn && umin == 0xFFFFFFFFu; w0 += 32 * kRC) {
-            uint32_t a[kRC], b[kRC];
+            load_ae(w0);
+            uint32_t bp[kRC];
 #pragma unroll
             for (int k = 0; k < kRC; ++k) {
                 const int w = w0 + k * 32 + lane;
-                a[k] = w < wn ? __ldg(rv + w) : 0u;
-                b[k] = w < wn ? __ldg(rp + w) : 0u;
+                bp[k] = w < wn ? __ldg(rp + w) : 0u;
             }
 #pragma unroll
             for (int k = 0; k < kRC; ++k) {
                 const int w = w0 + k * 32 + lane;
-                uint32_t bits = a[k] & ~b[k];
+                uint32_t bits = ae[k] & ~bp[k];
                 if (w == wn - 1) bits &= lastmask;
                 if (w == (p >> 5)) bits &= ~(1u << (p & 31));
-                while (bits && umin == 0xFFFFFFFFu) {
-                    const int u = (w << 5) + (__ffs(bits) - 1);
-                    bits &= bits - 1;
-                    if (__ldg(pos_g + u) < pv) umin = (unsigned)u;
+                if (E) {
+                    if (bits && umin == 0xFFFFFFFFu) umin = (unsigned)((w << 5) + __ffs(bits) - 1);
+                } else {
+                    while (bits && umin == 0xFFFFFFFFu) {
+                        const int u = (w << 5) + (__ffs(bits) - 1);
+                        bits &= bits - 1;
+                        if (__ldg(pos_g + u) < pv) umin = (unsigned)u;
+                    }
                 }
             }
             umin = __reduce_min_sync(0xFFFFFFFFu, umin);
         }
+        umin = min(umin, xmin);
         if (lane == 0 && umin != 0xFFFFFFFFu)
             atomicMin(keys + gi, ((unsigned long long)(unsigned)pv << 32) | umin);
+    }
+}
+
+// Flags an order that is not a permutation of 0..n-1 (seen[] zeroed).
+__global__ void order_check_kernel(int n, const int32_t *__restrict__ order, int *__restrict__ seen,
+                                   int *__restrict__ flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int x = order[i];
+        if (x < 0 || x >= n || atomicExch(&seen[x], 1) != 0) atomicOr(flag, 1);
+    }
+}
+
+// The check's preparation, one launch per bucket of graphs (blockIdx.y =
+// graph): blocks [0, mask_blocks) build E_b, one warp per tile of 32 words w
+// (a lane per word, holding the position groups pos(u) / 32 of its 32
+// vertices) by kMaskRows rows b, so the stores of a row are coalesced; with
+// PARENTS, the other blocks give each vertex v whose parent is not known yet
+// (all of them, or with prefilled those marked kParentUnresolved) a thread
+// that scans the kScan positions before pos(v), 8 independent probes at a
+// time, for the latest neighbour: p(v), -1 (none exists) or kParentUnresolved
+// (left to the check's warp).
+template <bool PARENTS>
+__global__ void peo_prep_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
+                                const int32_t *__restrict__ order, const int32_t *__restrict__ pos,
+                                int32_t *__restrict__ parent, uint32_t *__restrict__ emask, int mask_blocks,
+                                bool prefilled) {
+    const DenseDesc d = descs ? descs[blockIdx.y] : single;
+    const int n = d.n;
+    const int wn = (n + 31) >> 5;
+    const int32_t *pos_g = pos + d.vbase;
+    if ((int)blockIdx.x < mask_blocks) {
+        const int lane = threadIdx.x & 31;
+        const int wcols = (wn + 31) >> 5, brows = (wn + kMaskRows - 1) / kMaskRows;
+        const int64_t tiles = (int64_t)wcols * brows;
+        uint32_t *E = emask + d.ebase;
+        for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < tiles;
+             tile += ((int64_t)mask_blocks * blockDim.x) >> 5) {
+            const int wc = (int)(tile % wcols), br = (int)(tile / wcols);
+            const int w = (wc << 5) + lane;
+            uint32_t grp[32];   // position group of vertex 32 w + k (0xFFFFFFFF past n: never earlier)
+            if (w < wn && (w << 5) + 32 <= n && ((reinterpret_cast<uintptr_t>(pos_g) & 15) == 0)) {
+                const int4 *q = reinterpret_cast<const int4 *>(pos_g + (w << 5));
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int4 t4 = __ldg(q + k);
+                    grp[4 * k] = (uint32_t)t4.x >> 5;
+                    grp[4 * k + 1] = (uint32_t)t4.y >> 5;
+                    grp[4 * k + 2] = (uint32_t)t4.z >> 5;
+                    grp[4 * k + 3] = (uint32_t)t4.w >> 5;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const int u = (w << 5) + k;
+                    grp[k] = (w < wn && u < n) ? (uint32_t)__ldg(pos_g + u) >> 5 : 0xFFFFFFFFu;
+                }
+            }
+            const int b0 = br * kMaskRows, b1 = min(b0 + kMaskRows, wn);
+            for (int b = b0; b < b1; ++b) {
+                uint32_t word = 0u;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) word |= (grp[k] < (uint32_t)b ? 1u : 0u) << k;
+                if (w < wn) E[(size_t)b * wn + w] = word;
+            }
+        }
+        return;
+    }
+    if (!PARENTS) return;
+    const int32_t *ord_g = order + d.obase;
+    const int stride = (gridDim.x - mask_blocks) * blockDim.x;
+    for (int v = (blockIdx.x - mask_blocks) * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (prefilled && parent[d.vbase + v] != kParentUnresolved) continue;
+        const int pv = __ldg(pos_g + v);
+        if (pv < 0 || pv >= n) continue;   // skipped by the check as well
+        const uint32_t *rv = d.rows + (size_t)v * d.words;
+        const int jmin = max(0, pv - kScan);
+        int p = -1;
+        for (int j = pv - 1; j >= jmin && p < 0; j -= 8) {
+            int u[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) u[q] = j - q >= jmin ? __ldg(ord_g + j - q) : -1;
+            bool h[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) h[q] = (unsigned)u[q] < (unsigned)n && has_bit(rv, u[q]);
+#pragma unroll
+            for (int q = 7; q >= 0; --q)
+                if (h[q]) p = u[q];   // the latest (smallest q) wins
+        }
+        if (p < 0 && jmin > 0) p = kParentUnresolved;
+        parent[d.vbase + v] = p;
     }
 }
 
@@ -170,21 +352,53 @@ int invert_order_launch(const DenseDesc *descs, DenseDesc single, int count, con
     return CG_OK;
 }
 
+int order_check_launch(int n, const int32_t *order, int *seen, int *flag, int num_sms, cudaStream_t stream) {
+    CG_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), stream));
+    if (n <= 0) return CG_OK;
+    CG_CUDA_TRY(cudaMemsetAsync(seen, 0, sizeof(int) * (size_t)n, stream));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms * 4));
+    order_check_kernel<<<blocks, 256, 0, stream>>>(n, order, seen, flag);
+    CG_LAUNCH_CHECK("order_check_kernel");
+    return CG_OK;
+}
+
+int64_t earlier_mask_words(int n) {
+    const int64_t wn = (n + 31) / 32;
+    return wn * wn;
+}
+
 int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
                      const int32_t *order, const int32_t *pos, int32_t *parent, bool parent_known,
-                     unsigned long long *keys, int num_sms, cudaStream_t stream) {
+                     unsigned long long *keys, int num_sms, cudaStream_t stream, uint32_t *emask, int n_max,
+                     bool prefilled) {
     if (count <= 0) return CG_OK;
     CG_CUDA_TRY(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * count, stream));
     if (total <= 0) return CG_OK;
+    if (emask) {
+        if (count > 65535) return set_error(CG_EINVAL, "too many graphs for one mask launch (%d)", count);
+        const int64_t wn = (n_max + 31) / 32;
+        const int64_t tiles = ceil_div(wn, 32) * ceil_div(wn, kMaskRows);   // one warp per tile
+        const int mask_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(tiles, 8), (int64_t)num_sms * 4));
+        const int parent_blocks =
+            parent_known ? 0 : (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n_max, 256), (int64_t)num_sms * 4));
+        const dim3 grid(mask_blocks + parent_blocks, count);
+        if (parent_known)
+            peo_prep_kernel<false><<<grid, 256, 0, stream>>>(descs, single, order, pos, parent, emask, mask_blocks,
+                                                             false);
+        else
+            peo_prep_kernel<true><<<grid, 256, 0, stream>>>(descs, single, order, pos, parent, emask, mask_blocks,
+                                                            prefilled);
+        CG_LAUNCH_CHECK("peo_prep_kernel");
+    }
     const int64_t warps_needed = total;
     const int64_t blocks_needed = ceil_div(warps_needed, kPeoThreads / 32);
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, (int64_t)num_sms * 8));
     if (parent_known)
         peo_dense_kernel<true><<<blocks, kPeoThreads, 0, stream>>>(descs, single, count, voff, total, order, pos,
-                                                                   parent, keys);
+                                                                   parent, emask, keys);
     else
         peo_dense_kernel<false><<<blocks, kPeoThreads, 0, stream>>>(descs, single, count, voff, total, order, pos,
-                                                                    parent, keys);
+                                                                    parent, emask, keys);
     CG_LAUNCH_CHECK("peo_dense_kernel");
     return CG_OK;
 }

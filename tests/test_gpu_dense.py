@@ -166,6 +166,42 @@ def test_peo_check_of_given_orders(ctx):
             assert np.array_equal(parent.cpu().numpy(), want.parent)
 
 
+@pytest.mark.parametrize("n", [8191, 8192, 8193, 16384, 20000])
+def test_peo_check_multi_chunk(ctx, n):
+    """Rows longer than one register chunk; random orders put parents far
+    back (the mask binary search), LexBFS orders close (the probes)."""
+    rs = np.random.Generator(np.random.PCG64(n))
+    g = gg.random_dense(n, 0.02, n + 1)
+    h = gg.subtree_dense(n, n // 8, n + 2)
+    for G, order in ((g, rs.permutation(n)), (h, rs.permutation(n)), (h, oracle.lexbfs(h))):
+        order = order.astype(np.int32)
+        want = oracle.peo_check(G, order)
+        res = torch.empty(4, dtype=torch.int32, device=DEV)
+        parent = torch.empty(n, dtype=torch.int32, device=DEV)
+        B.peo_check_dense(ctx, to_dev(G), n, torch.from_numpy(order).to(DEV), res, parent)
+        torch.cuda.synchronize()
+        assert tuple(res.cpu().tolist()) == want.witness
+        assert np.array_equal(parent.cpu().numpy(), want.parent)
+
+
+def test_peo_check_validates_order():
+    c = B.Context(0, validate=1)
+    try:
+        g = gg.random_dense(100, 0.1, 3)
+        rows = to_dev(g)
+        res = torch.empty(4, dtype=torch.int32, device=DEV)
+        bad = np.arange(100, dtype=np.int32)
+        bad[5] = 6
+        with pytest.raises(Exception):
+            B.peo_check_dense(c, rows, 100, torch.from_numpy(bad).to(DEV), res)
+        good = np.random.Generator(np.random.PCG64(1)).permutation(100).astype(np.int32)
+        B.peo_check_dense(c, rows, 100, torch.from_numpy(good).to(DEV), res)
+        torch.cuda.synchronize()
+        assert tuple(res.cpu().tolist()) == oracle.peo_check(g, good).witness
+    finally:
+        c.close()
+
+
 def test_host_entry(ctx):
     g, h, _ = gg.small_dense_pair()
     for G in (g, h, gg.empty_dense(0), gg.cycle(4)):
