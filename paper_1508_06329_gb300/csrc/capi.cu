@@ -232,7 +232,7 @@ BatchBuffers batch_buffers(const BatchLayout &L, bool need_order) {
     bb.o_order = cv.take<int32_t>(need_order ? L.total : 0);
     bb.o_pos = cv.take<int32_t>(L.total);
     bb.o_parent = cv.take<int32_t>(L.total);
-    bb.o_keys = cv.take<unsigned long long>(L.count);
+    bb.o_keys = cv.take<unsigned long long>(L.count + 1);   // + the check's block counter (bucket 9 is last)
     bb.o_counter = cv.take<int>(kBuckets * 64);
     const auto &B9 = L.bk[9];
     bb.o_gstate = cv.take<unsigned char>(B9.end > B9.begin ? B9.lplan.gstate_bytes * B9.ctas : 0);
@@ -282,11 +282,9 @@ int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
             // the check over this bucket's vertices (a slice of the offset table)
             if ((rc = peo_dense_launch(ddesc + B.begin, DenseDesc{}, cnt, dvoff + B.begin, B.vend - B.vbegin, order,
                                        pos, parent, false, keys + B.begin, ctx->num_sms, s,
-                                       reinterpret_cast<uint32_t *>(P(bb.o_emask)), B.nmax, true)))
+                                       reinterpret_cast<uint32_t *>(P(bb.o_emask)), B.nmax, true, res)))
                 return rc;
-            if ((rc = finalize_launch(ddesc + B.begin, DenseDesc{}, cnt, keys + B.begin, order, parent, res, s)))
-                return rc;
-            if (account) ctx->launches += 4;
+            if (account) ctx->launches += 3;
         }
         CG_CUDA_TRY(cudaEventRecord(ss.join[b], s));
         CG_CUDA_TRY(cudaStreamWaitEvent(stream, ss.join[b], 0));
@@ -328,7 +326,7 @@ struct SingleDenseCarve {
         o_order = cv.take<int32_t>(n);
         o_pos = cv.take<int32_t>(n);
         o_parent = cv.take<int32_t>(n);
-        o_key = cv.take<unsigned long long>(1);
+        o_key = cv.take<unsigned long long>(2);
         o_counter = cv.take<int>(1);
         o_gstate = cv.take<unsigned char>(plan.gstate_bytes);
         o_emask = cv.take<uint32_t>(earlier_mask_words(n));
@@ -363,11 +361,9 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
     if (!res) return CG_OK;
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
     unsigned long long *key = at<unsigned long long>(ctx, o_key);
-    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream,
-                               at<uint32_t>(ctx, o_emask), n, true)))
-        return rc;
-    ctx->launches += n > 0 ? 3 : 1;
-    return finalize_launch(nullptr, d, 1, key, order, parent, res, stream);
+    ctx->launches += n > 0 ? 2 : 1;
+    return peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream,
+                            at<uint32_t>(ctx, o_emask), n, true, res);
 }
 
 // Optional layout check of a CSR graph (synchronises the stream).
@@ -565,7 +561,7 @@ int cg_peo_check_dense(cg_context *ctx, const cg_dense *g, const int32_t *order,
     Carve cv;
     const size_t o_pos = cv.take<int32_t>(n);
     const size_t o_parent = cv.take<int32_t>(n);
-    const size_t o_key = cv.take<unsigned long long>(1);
+    const size_t o_key = cv.take<unsigned long long>(2);
     const size_t o_emask = cv.take<uint32_t>(earlier_mask_words(n));
     const size_t o_flag = cv.take<int>(1);
     if ((rc = ensure_ws(ctx, cv.off))) return rc;
@@ -584,11 +580,9 @@ int cg_peo_check_dense(cg_context *ctx, const cg_dense *g, const int32_t *order,
     // vertices missing from an invalid order keep position -1 and are skipped
     if (n > 0) CG_CUDA_TRY(cudaMemsetAsync(pos, 0xFF, sizeof(int32_t) * (size_t)n, stream));
     if ((rc = invert_order_launch(nullptr, d, 1, nullptr, n, order, pos, ctx->num_sms, stream))) return rc;
-    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, par, false, key, ctx->num_sms, stream,
-                               at<uint32_t>(ctx, o_emask), n)))
-        return rc;
-    ctx->launches += n > 0 ? 4 : 1;
-    return finalize_launch(nullptr, d, 1, key, order, par, res, stream);
+    ctx->launches += n > 0 ? 3 : 1;
+    return peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, par, false, key, ctx->num_sms, stream,
+                            at<uint32_t>(ctx, o_emask), n, false, res);
 }
 
 int cg_chordal_test_dense_host(cg_context *ctx, int32_t n, int32_t words_per_row, const uint32_t *host_rows,
@@ -629,7 +623,7 @@ int run_mcs_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int32_
     const size_t o_order = cv.take<int32_t>(n);
     const size_t o_pos = cv.take<int32_t>(n);
     const size_t o_parent = cv.take<int32_t>(n);
-    const size_t o_key = cv.take<unsigned long long>(1);
+    const size_t o_key = cv.take<unsigned long long>(2);
     const size_t o_counter = cv.take<int>(1);
     const size_t o_emask = cv.take<uint32_t>(res ? earlier_mask_words(n) : 0);
     int rc;
@@ -646,11 +640,9 @@ int run_mcs_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int32_
     if (!res) return CG_OK;
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
     unsigned long long *key = at<unsigned long long>(ctx, o_key);
-    if ((rc = peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream,
-                               at<uint32_t>(ctx, o_emask), n)))
-        return rc;
-    ctx->launches += n > 0 ? 3 : 1;
-    return finalize_launch(nullptr, d, 1, key, order, parent, res, stream);
+    ctx->launches += n > 0 ? 2 : 1;
+    return peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream,
+                            at<uint32_t>(ctx, o_emask), n, false, res);
 }
 }  // namespace
 

@@ -41,10 +41,13 @@ int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc s
 // words at each desc's ebase; n_max = the largest n), or null for the
 // gather-based check.  prefilled (with masks, parent_known false): parent
 // already holds p(v) or kParentUnresolved for each v (from the search).
+// res: when given, the results are written too (keys then needs count + 1
+// entries: the last counts the check's finished blocks); otherwise the
+// caller runs finalize_launch.
 int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
                      const int32_t *order, const int32_t *pos, int32_t *parent, bool parent_known,
                      unsigned long long *keys, int num_sms, cudaStream_t stream, uint32_t *emask = nullptr,
-                     int n_max = 0, bool prefilled = false);
+                     int n_max = 0, bool prefilled = false, cg_result *res = nullptr);
 int64_t earlier_mask_words(int n);
 // sets *flag when order is not a permutation of 0..n-1 (seen: n ints of scratch)
 int order_check_launch(int n, const int32_t *order, int *seen, int *flag, int num_sms, cudaStream_t stream);

@@ -35,6 +35,22 @@ constexpr int kRC = 8;    // row words per lane held in registers (256 words = 8
 constexpr int kMaskRows = 32;         // rows b per mask tile
 constexpr int kScan = 32;             // positions a prep thread scans for p(v)
 
+// (chordal, v, p, u) from a graph's key (pos(v*) << 32 | u*, or ~0 when chordal).
+__device__ __forceinline__ void write_result(const DenseDesc &d, unsigned long long k, const int32_t *order,
+                                             const int32_t *parent, cg_result *out) {
+    cg_result r;
+    if (k == ~0ull) {
+        r.chordal = 1;
+        r.v = r.p = r.u = -1;
+    } else {
+        r.chordal = 0;
+        r.v = order[d.obase + (int)(k >> 32)];
+        r.p = parent[d.vbase + r.v];
+        r.u = (int)(k & 0xFFFFFFFFu);
+    }
+    *out = r;
+}
+
 // p(v) by gathering pos over every neighbour: max pos(u) < pos(v).
 __device__ __forceinline__ int parent_by_gather(const uint32_t *__restrict__ rv, int wn, uint32_t lastmask,
                                                 const int32_t *__restrict__ pos_g, int pv, int lane) {
@@ -78,7 +94,8 @@ __global__ void __launch_bounds__(kPeoThreads, 4) peo_dense_kernel(const DenseDe
                                                                 const int32_t *__restrict__ pos,
                                                                 int32_t *__restrict__ parent,
                                                                 const uint32_t *__restrict__ emask,
-                                                                unsigned long long *__restrict__ keys) {
+                                                                unsigned long long *__restrict__ keys,
+                                                                cg_result *__restrict__ res) {
     constexpr int kProbe = 4;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -205,6 +222,21 @@ __global__ void __launch_bounds__(kPeoThreads, 4) peo_dense_kernel(const DenseDe
         if (lane == 0 && umin != 0xFFFFFFFFu)
             atomicMin(keys + gi, ((unsigned long long)(unsigned)pv << 32) | umin);
     }
+    if (res) {   // the last block to finish turns the keys into results (keys[count] counts blocks)
+        __shared__ bool last;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            last = atomicAdd(keys + count, 1ull) == (unsigned long long)gridDim.x - 1;
+        }
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            for (int g = threadIdx.x; g < count; g += blockDim.x)
+                write_result(descs ? descs[g] : single, atomicAdd(keys + g, 0ull), order, parent,
+                             res + (descs ? descs[g].rindex : g));
+        }
+    }
 }
 
 // Flags an order that is not a permutation of 0..n-1 (seen[] zeroed).
@@ -229,7 +261,11 @@ template <bool PARENTS>
 __global__ void peo_prep_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
                                 const int32_t *__restrict__ order, const int32_t *__restrict__ pos,
                                 int32_t *__restrict__ parent, uint32_t *__restrict__ emask, int mask_blocks,
-                                bool prefilled) {
+                                bool prefilled, unsigned long long *__restrict__ keys) {
+    if (keys && blockIdx.x == 0 && threadIdx.x == 0) {   // "no violation" key, and the check's block counter
+        keys[blockIdx.y] = ~0ull;
+        if (blockIdx.y == 0) keys[gridDim.y] = 0ull;
+    }
     const DenseDesc d = descs ? descs[blockIdx.y] : single;
     const int n = d.n;
     const int wn = (n + 31) >> 5;
@@ -303,19 +339,7 @@ __global__ void finalize_kernel(const DenseDesc *__restrict__ descs, DenseDesc s
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= count) return;
     const DenseDesc d = descs ? descs[gi] : single;
-    const unsigned long long k = keys[gi];
-    cg_result r;
-    if (k == ~0ull) {
-        r.chordal = 1;
-        r.v = r.p = r.u = -1;
-    } else {
-        const int pv = (int)(k >> 32);
-        r.chordal = 0;
-        r.v = order[d.obase + pv];
-        r.p = parent[d.vbase + r.v];
-        r.u = (int)(k & 0xFFFFFFFFu);
-    }
-    res[descs ? d.rindex : gi] = r;
+    write_result(d, keys[gi], order, parent, res + (descs ? d.rindex : gi));
 }
 
 __global__ void invert_order_kernel(const DenseDesc *__restrict__ descs, DenseDesc single, int count,
@@ -370,10 +394,11 @@ int64_t earlier_mask_words(int n) {
 int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
                      const int32_t *order, const int32_t *pos, int32_t *parent, bool parent_known,
                      unsigned long long *keys, int num_sms, cudaStream_t stream, uint32_t *emask, int n_max,
-                     bool prefilled) {
+                     bool prefilled, cg_result *res) {
     if (count <= 0) return CG_OK;
-    CG_CUDA_TRY(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * count, stream));
-    if (total <= 0) return CG_OK;
+    const bool fused = emask && res && total > 0;   // keys initialised by the prep kernel, results by the check
+    if (!fused) CG_CUDA_TRY(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * count, stream));
+    if (total <= 0) return res ? finalize_launch(descs, single, count, keys, order, parent, res, stream) : CG_OK;
     if (emask) {
         if (count > 65535) return set_error(CG_EINVAL, "too many graphs for one mask launch (%d)", count);
         const int64_t wn = (n_max + 31) / 32;
@@ -382,24 +407,27 @@ int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const 
         const int parent_blocks =
             parent_known ? 0 : (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n_max, 256), (int64_t)num_sms * 4));
         const dim3 grid(mask_blocks + parent_blocks, count);
+        unsigned long long *kinit = fused ? keys : nullptr;
         if (parent_known)
             peo_prep_kernel<false><<<grid, 256, 0, stream>>>(descs, single, order, pos, parent, emask, mask_blocks,
-                                                             false);
+                                                             false, kinit);
         else
             peo_prep_kernel<true><<<grid, 256, 0, stream>>>(descs, single, order, pos, parent, emask, mask_blocks,
-                                                            prefilled);
+                                                            prefilled, kinit);
         CG_LAUNCH_CHECK("peo_prep_kernel");
     }
     const int64_t warps_needed = total;
     const int64_t blocks_needed = ceil_div(warps_needed, kPeoThreads / 32);
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, (int64_t)num_sms * 8));
+    cg_result *fres = fused ? res : nullptr;
     if (parent_known)
         peo_dense_kernel<true><<<blocks, kPeoThreads, 0, stream>>>(descs, single, count, voff, total, order, pos,
-                                                                   parent, emask, keys);
+                                                                   parent, emask, keys, fres);
     else
         peo_dense_kernel<false><<<blocks, kPeoThreads, 0, stream>>>(descs, single, count, voff, total, order, pos,
-                                                                    parent, emask, keys);
+                                                                    parent, emask, keys, fres);
     CG_LAUNCH_CHECK("peo_dense_kernel");
+    if (res && !fused) return finalize_launch(descs, single, count, keys, order, parent, res, stream);
     return CG_OK;
 }
 
