@@ -184,8 +184,8 @@ def make_workload(name: str):
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the current kernel (profiles/lexbfs_dense_n16384_pair.txt):
-# lexbfs_dense_kernel on the N=16,384 pair, 67.79 MB read + 1.87 MB written.
-NCU_TRAFFIC_BYTES = {"dense16k": 67.79e6 + 1.87e6}
+# lexbfs_dense_kernel on the N=16,384 pair, 68.39 MB read + 1.51 MB written.
+NCU_TRAFFIC_BYTES = {"dense16k": 68.39e6 + 1.51e6}
 
 
 def algorithmic_bytes(g) -> int:
