@@ -130,6 +130,14 @@ enum { CG_TIE_ID = 0, CG_TIE_RANK = 1, CG_TIE_LAST_IN = 2 };
 int cg_lexbfs_sweep_dense(cg_context *ctx, const cg_dense *g, int32_t kind, const int32_t *tiebreak, int32_t start,
                           int32_t *order, int32_t *pos, cudaStream_t stream);
 
+/* The same sweep on a CSR graph (any n the CSR LexBFS takes).  The relabelled
+ * copy (new rows renamed and sorted again on the GPU) takes workspace of
+ * about 16 (n + 1) + 12 nnz bytes besides the CSR LexBFS state.  tiebreak,
+ * start, order and pos as for cg_lexbfs_sweep_dense; cfg.validate also checks
+ * the CSR layout. */
+int cg_lexbfs_sweep_csr(cg_context *ctx, const cg_csr *g, int32_t kind, const int32_t *tiebreak, int32_t start,
+                        int32_t *order, int32_t *pos, cudaStream_t stream);
+
 /*
  * Perfect-elimination check of a caller-given order (Sections 5.2 and 6.2):
  * p(v) = the neighbour of v with the largest order index below v's, then

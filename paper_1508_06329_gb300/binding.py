@@ -86,6 +86,7 @@ SIGNATURES = {
     "cg_chordal_test_dense_host": ([P, I32, I32, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_batch": ([P, P, I32, P, P, P, P], ctypes.c_int),
     "cg_lexbfs_sweep_dense": ([P, P, ctypes.c_int32, P, ctypes.c_int32, P, P, P], ctypes.c_int),
+    "cg_lexbfs_sweep_csr": ([P, P, ctypes.c_int32, P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "cg_mcs_order_dense": ([P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_mcs_dense": ([P, P, P, P, P], ctypes.c_int),
     "cg_lexbfs_order_csr": ([P, P, P, P, P], ctypes.c_int),
@@ -154,6 +155,7 @@ cg_chordal_test_dense = _fn("cg_chordal_test_dense")
 cg_chordal_test_dense_host = _fn("cg_chordal_test_dense_host")
 cg_chordal_test_batch = _fn("cg_chordal_test_batch")
 cg_lexbfs_sweep_dense = _fn("cg_lexbfs_sweep_dense")
+cg_lexbfs_sweep_csr = _fn("cg_lexbfs_sweep_csr")
 cg_mcs_order_dense = _fn("cg_mcs_order_dense")
 cg_chordal_test_mcs_dense = _fn("cg_chordal_test_mcs_dense")
 cg_lexbfs_order_csr = _fn("cg_lexbfs_order_csr")
@@ -312,6 +314,18 @@ def csr_desc(row_ptr, col, n: int) -> cg_csr:
 def lexbfs_order_csr(ctx: Context, row_ptr, col, n: int, order, pos=None, stream=None):
     d = csr_desc(row_ptr, col, n)
     _check(cg_lexbfs_order_csr(ctx.handle, ctypes.byref(d), _ptr(order), _ptr(pos), _stream(stream)))
+
+
+def lexbfs_sweep_csr(ctx: Context, row_ptr, col, n: int, order, pos=None, kind: int = TIE_ID, tiebreak=None,
+                     start: int = -1, stream=None):
+    d = csr_desc(row_ptr, col, n)
+    _check(cg_lexbfs_sweep_csr(ctx.handle, ctypes.byref(d), kind, _ptr(tiebreak), start, _ptr(order), _ptr(pos),
+                               _stream(stream)))
+
+
+def lexbfs_plus_csr(ctx: Context, row_ptr, col, n: int, prev_order, order, pos=None, start: int = -1, stream=None):
+    """LexBFS+ of a previous sweep on a CSR graph."""
+    lexbfs_sweep_csr(ctx, row_ptr, col, n, order, pos, TIE_LAST_IN, prev_order, start, stream)
 
 
 def chordal_test_csr(ctx: Context, row_ptr, col, n: int, res, order=None, stream=None):

@@ -544,6 +544,49 @@ int cg_lexbfs_sweep_dense(cg_context *ctx, const cg_dense *g, int32_t kind, cons
     return CG_OK;
 }
 
+int cg_lexbfs_sweep_csr(cg_context *ctx, const cg_csr *g, int32_t kind, const int32_t *tiebreak, int32_t start,
+                        int32_t *order, int32_t *pos, cudaStream_t stream) {
+    int rc;
+    if ((rc = check_ctx(ctx)) || (rc = check_csr(g))) return rc;
+    const int n = g->n;
+    if (n > 0 && !order) return set_error(CG_EINVAL, "null order pointer");
+    if (kind != CG_TIE_ID && kind != CG_TIE_RANK && kind != CG_TIE_LAST_IN)
+        return set_error(CG_EINVAL, "unknown tie-break kind %d", kind);
+    if (kind != CG_TIE_ID && n > 0 && !tiebreak) return set_error(CG_EINVAL, "null tie-break array");
+    if (start < -1 || (start >= 0 && start >= n)) return set_error(CG_EINVAL, "start %d outside [-1, n)", start);
+    if (kind == CG_TIE_ID && start < 0) return run_single_csr(ctx, g, order, pos, nullptr, stream);
+    if (n == 0) return CG_OK;
+    Carve cv;
+    const size_t o_rank = cv.take<int32_t>(n), o_newid = cv.take<int32_t>(n), o_inv = cv.take<int32_t>(n);
+    const size_t o_seen = cv.take<int>(n), o_order = cv.take<int32_t>(n), o_pos = cv.take<int32_t>(n);
+    const size_t o_flag = cv.take<int>(1);
+    const size_t o_state = cv.take<unsigned char>(lexbfs_csr_workspace_bytes(n, n));
+    const size_t o_relabel = cv.take<unsigned char>(sweep_csr_workspace_bytes(n, g->nnz));
+    if ((rc = ensure_ws(ctx, cv.off))) return rc;
+    if (ctx->cfg.validate && (rc = validate_csr(ctx, g, at<int>(ctx, o_flag), stream))) return rc;
+    SweepBuffers sb{nullptr, at<int32_t>(ctx, o_rank), at<int32_t>(ctx, o_newid), at<int32_t>(ctx, o_inv),
+                    at<int>(ctx, o_seen), at<int32_t>(ctx, o_order), at<int32_t>(ctx, o_pos), at<int>(ctx, o_flag)};
+    PhaseTimer pt(ctx, &ctx->ev_lex, stream);
+    if ((rc = sweep_ids_launch(n, kind, tiebreak, start, sb, ctx->num_sms, stream))) return rc;
+    if (ctx->cfg.validate) {
+        int flag = 0;
+        CG_CUDA_TRY(cudaMemcpyAsync(&flag, sb.flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CG_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (flag) return set_error(CG_EINVAL, "tie-break array is not a permutation of 0..n-1");
+    }
+    int64_t *rp_new = nullptr;
+    int32_t *col_new = nullptr;
+    if ((rc = sweep_csr_relabel_launch(n, g->nnz, g->row_ptr, g->col, sb, at<void>(ctx, o_relabel), &rp_new,
+                                       &col_new, ctx->num_sms, stream)))
+        return rc;
+    if ((rc = lexbfs_csr_launch(n, n, rp_new, col_new, sb.order_p, sb.pos_p, nullptr, at<void>(ctx, o_state),
+                                ctx->num_sms, stream)))
+        return rc;
+    if ((rc = sweep_unpermute_launch(n, sb, order, pos, ctx->num_sms, stream))) return rc;
+    ctx->launches += 14;
+    return CG_OK;
+}
+
 int cg_chordal_test_dense(cg_context *ctx, const cg_dense *g, cg_result *res, int32_t *order, cudaStream_t stream) {
     int rc;
     if ((rc = check_ctx(ctx)) || (rc = check_dense(g))) return rc;

@@ -87,6 +87,13 @@ struct SweepBuffers {
 // new ids from the tie-break array (sets *sb.flag if it is not a permutation)
 int sweep_ids_launch(int n, int kind, const int32_t *tiebreak, int start, const SweepBuffers &sb, int num_sms,
                      cudaStream_t stream);
+// order[i] = inv[order_p[i]], pos[v] = pos_p[newid[v]]
+int sweep_unpermute_launch(int n, const SweepBuffers &sb, int32_t *order, int32_t *pos, int num_sms,
+                           cudaStream_t stream);
+// ---- the CSR sweep's relabelled copy (sweep_csr.cu): rows renamed by newid and sorted
+size_t sweep_csr_workspace_bytes(int64_t n, int64_t nnz);
+int sweep_csr_relabel_launch(int n, int64_t nnz, const int64_t *row_ptr, const int32_t *col, const SweepBuffers &sb,
+                             void *ws, int64_t **rp_new, int32_t **col_new, int num_sms, cudaStream_t stream);
 // relabelled matrix, LexBFS on it, order / pos mapped back
 int sweep_order_launch(const DenseDesc &d, const LexPlan &plan, void *gstate, int *counter, const SweepBuffers &sb,
                        int32_t *order, int32_t *pos, int num_sms, cudaStream_t stream);

@@ -91,7 +91,10 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
         const size_t rows = (size_t)n * wn * 4;
         p.wide_ids = false;
         p.rows_smem = kLexScalarBytes + state + rows <= kSmemLimit;
-        int th = n <= 512 ? 128 : (n <= 2048 ? 256 : (n <= 8192 ? 512 : 1024));
+        // measured on GB300 (subtree, clique, tree, G(n, 0.1) graphs): 512 threads
+        // up to ~1,500 vertices, 1024 above (more lanes per row word shorten the
+        // per-step bit loops more than the extra warps cost at the barriers)
+        int th = n <= 1536 ? 512 : 1024;
         if (threads_override) th = threads_override;
         // words per thread must cover the row
         while ((int64_t)th * (th == 128 ? 4 : th == 256 ? 2 : 1) < wn) th *= 2;

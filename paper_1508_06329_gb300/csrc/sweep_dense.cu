@@ -115,6 +115,15 @@ int sweep_ids_launch(int n, int kind, const int32_t *tiebreak, int start, const 
     return CG_OK;
 }
 
+int sweep_unpermute_launch(int n, const SweepBuffers &sb, int32_t *order, int32_t *pos, int num_sms,
+                           cudaStream_t stream) {
+    if (n <= 0) return CG_OK;
+    const int blocks = (int)std::min<int64_t>(ceil_div((int64_t)n, 256), (int64_t)num_sms * 4);
+    sweep_unpermute_kernel<<<blocks, 256, 0, stream>>>(n, sb.newid, sb.inv, sb.order_p, sb.pos_p, order, pos);
+    CG_LAUNCH_CHECK("sweep_unpermute_kernel");
+    return CG_OK;
+}
+
 int sweep_order_launch(const DenseDesc &d, const LexPlan &plan, void *gstate, int *counter, const SweepBuffers &sb,
                        int32_t *order, int32_t *pos, int num_sms, cudaStream_t stream) {
     const int n = d.n;

@@ -94,3 +94,61 @@ def test_sweep_rejects_bad_input():
         assert np.array_equal(ok, oracle.lexbfs_tiebreak(g, np.arange(50, dtype=np.int32), -1))
     finally:
         c.close()
+
+
+# ----------------------------------------------------------------- CSR sweeps
+
+def sweep_csr(ctx, g, kind, tb, start):
+    n = g.n
+    rp = torch.from_numpy(np.ascontiguousarray(g.row_ptr, dtype=np.int64)).to(DEV)
+    col = torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).to(DEV)
+    if col.numel() == 0:
+        col = torch.zeros(1, dtype=torch.int32, device=DEV)[:0]
+    order = torch.full((max(n, 1),), -7, dtype=torch.int32, device=DEV)
+    pos = torch.full((max(n, 1),), -7, dtype=torch.int32, device=DEV)
+    tbd = None if tb is None else torch.from_numpy(np.ascontiguousarray(tb, dtype=np.int32)).to(DEV)
+    B.lexbfs_sweep_csr(ctx, rp, col, n, order, pos, kind, tbd, start)
+    torch.cuda.synchronize()
+    o, p = order[:n].cpu().numpy(), pos[:n].cpu().numpy()
+    inv = np.empty(n, np.int32)
+    inv[o] = np.arange(n)
+    assert np.array_equal(p, inv)
+    return o
+
+
+def hub_graph(n, seed):
+    """Random sparse graph plus a vertex adjacent to everything: rows of every
+    size class (<= 32, <= 4096 and longer) in the relabelled copy."""
+    g = gg.random_dense(n, 8.0 / n, seed)
+    rows = g.rows.copy()
+    hub = n // 3
+    for v in range(n):
+        if v != hub:
+            rows[hub, v >> 5] |= np.uint32(1 << (v & 31))
+            rows[v, hub >> 5] |= np.uint32(1 << (hub & 31))
+    return gg.dense_to_csr(gg.DenseGraph(n, rows))
+
+
+@pytest.mark.parametrize("n", [1, 2, 40, 1000, 9000])
+def test_sweep_csr_rank_and_start(ctx, n):
+    graphs = [gg.dense_to_csr(gg.random_dense(n, 0.05, n)), gg.dense_to_csr(gg.subtree_dense(n, max(2, n // 4), n + 1))]
+    if n >= 1000:
+        graphs.append(hub_graph(n, n + 2))
+    for s, g in enumerate(graphs):
+        rank = np.random.default_rng(n + s).permutation(n).astype(np.int32)
+        for start in (-1, n // 2):
+            got = sweep_csr(ctx, g, B.TIE_RANK, rank, start)
+            assert np.array_equal(got, oracle.lexbfs_tiebreak(g, rank, start)), (n, s, start)
+
+
+def test_sweep_csr_plus_chain_large(ctx):
+    """LexBFS+ sweeps on the N = 65,536 reversed-PEO CSR graph (a hub with a
+    few thousand neighbours), each fed the previous sweep."""
+    g, _, _ = gg.sparse_csr_pair(n=1 << 16)
+    prev = oracle.lexbfs(g)
+    got_prev = prev.astype(np.int32)
+    for _ in range(2):
+        want = oracle.lexbfs_plus(g, prev)
+        got = sweep_csr(ctx, g, B.TIE_LAST_IN, got_prev, -1)
+        assert np.array_equal(got, want)
+        prev, got_prev = want, got
