@@ -20,8 +20,9 @@ Other workloads (same JSON line; not run by default):
              density U[0.01, 0.2], dense below N = 8,192, CSR above; arrival
              rate 0.8 x the measured saturation throughput; p50 / p99 latency
 
-`--workload sweep16k` times one multi-sweep LexBFS sweep (LexBFS+ of the
-plain LexBFS order) on each graph of the N=16,384 pair; unit sweeps/s.
+`--workload sweep16k` / `sweep1m` time one multi-sweep LexBFS sweep (LexBFS+
+of the plain LexBFS order) on each graph of the dense N=16,384 pair / the CSR
+N=2^20 pair; unit sweeps/s.
 
 `--order mcs` (dense16k, small1k) runs the same test with the Maximum
 Cardinality Search order (Section 5.1) instead of LexBFS: one graph per call,
@@ -154,6 +155,12 @@ def make_workload(name: str):
                                     "(subtree-intersection chordal graph, density %.3f, + %d cycle-closing edges); "
                                     "previous sweep = the plain LexBFS order" % (g.density(), info["r"]),
                         "n": g.n, "words_per_row": g.words, "graphs_per_step": 2}
+    if name == "sweep1m":
+        g, h, info = gg.sparse_csr_pair()
+        return [g, h], {"workload": "one LexBFS+ sweep (multi-sweep LexBFS) of each graph of the CSR N=2^20 pair "
+                                    "(reversed-PEO chordal graph + %d cycle-closing edges); previous sweep = the "
+                                    "plain LexBFS order" % info["r"],
+                        "n": g.n, "graphs_per_step": 2, "edges": [g.num_edges(), h.num_edges()]}
     if name == "small1k":
         g, h, info = gg.small_dense_pair()
         return [g, h], {"workload": "dense N=1000 subtree-intersection chordal graph (500-node tree) + copy with a "
@@ -262,7 +269,7 @@ def run_reference(args):
     if args.order == "mcs":
         cfg = dict(cfg, order="MCS (Section 5.1)")
     test = oracle_test_fn(args.order)
-    if args.workload == "sweep16k":
+    if args.workload in ("sweep16k", "sweep1m"):
         import oracle
         prev = {id(g): oracle.lexbfs(g) for g in graphs}
 
@@ -279,12 +286,13 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = len(sample) * args.steps / total
-    unit = UNIT if args.workload != "sweep16k" else "sweeps/s"
+    unit = UNIT if not args.workload.startswith("sweep") else "sweeps/s"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 bitsets / int32",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT if args.workload != "sweep16k" else "sweeps/s", "cores": 1,
+            "cpu_baseline": {"value": value, "unit": UNIT if not args.workload.startswith("sweep") else "sweeps/s",
+                             "cores": 1,
                              "kind": "oracle",
                              "sample": f"{args.steps} steps x {len(sample)} graphs of the workload, "
                                        "single-threaded C oracle"},
@@ -494,9 +502,10 @@ def run_paper7(args):
 
 
 def run_sweep(args):
-    """One LexBFS+ sweep per graph of the N=16,384 pair (two streams), each
-    fed the plain LexBFS order as the previous sweep; the sweep relabels the
-    graph on the GPU and runs the dense LexBFS on the copy."""
+    """One LexBFS+ sweep per graph of the N=16,384 dense pair (sweep16k) or the
+    N=2^20 CSR pair (sweep1m), two streams, each fed the plain LexBFS order as
+    the previous sweep; the sweep relabels the graph on the GPU and runs the
+    LexBFS on the copy."""
     import numpy as np
     import torch
     import oracle
@@ -509,10 +518,14 @@ def run_sweep(args):
     from paper_1508_06329_gb300 import build as cbuild
     cbuild.build()
     from paper_1508_06329_gb300 import binding as B
-    graphs, cfg = make_workload("sweep16k")
+    graphs, cfg = make_workload(args.workload)
+    dense = hasattr(graphs[0], "rows")
     prev_h = [oracle.lexbfs(g) for g in graphs]
     want = [oracle.lexbfs_plus(g, p) for g, p in zip(graphs, prev_h)]
-    rows = [torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).to(dev) for g in graphs]
+    if dense:
+        rows = [torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).to(dev) for g in graphs]
+    else:
+        rows = [(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev)) for g in graphs]
     prev = [torch.from_numpy(p.astype(np.int32)).to(dev) for p in prev_h]
     orders = [torch.empty(g.n, dtype=torch.int32, device=dev) for g in graphs]
     stream = torch.cuda.current_stream()
@@ -525,10 +538,14 @@ def run_sweep(args):
         ev.record(stream)
         for k, g in enumerate(graphs):
             side[k].wait_event(ev)
-            if plain:
+            if dense and plain:
                 B.lexbfs_order_dense(ctxs[k], rows[k], g.n, orders[k], None, side[k])
-            else:
+            elif dense:
                 B.lexbfs_plus_dense(ctxs[k], rows[k], g.n, prev[k], orders[k], None, stream=side[k])
+            elif plain:
+                B.lexbfs_order_csr(ctxs[k], rows[k][0], rows[k][1], g.n, orders[k], None, side[k])
+            else:
+                B.lexbfs_plus_csr(ctxs[k], rows[k][0], rows[k][1], g.n, prev[k], orders[k], None, stream=side[k])
         for s_ in side:
             stream.wait_stream(s_)
 
@@ -544,7 +561,7 @@ def run_sweep(args):
             ms.append(a.elapsed_time(b))
         return ms
 
-    warm = max(args.warmup, 3)
+    warm = max(args.warmup, 3) if dense else 1
     timed(False, warm)
     for k in range(len(graphs)):
         if not np.array_equal(orders[k].cpu().numpy(), want[k]):
@@ -567,17 +584,23 @@ def run_sweep(args):
             prof[k] = prof.get(k, 0) + v
         c.profile(False)
     total_ms, value = aggregate_over_ranks(sum(ms), len(graphs) * args.steps, dev)
-    plain_ms = timed(True, max(3, min(args.steps, 5)))
+    plain_ms = timed(True, max(3, min(args.steps, 5)) if dense else 1)
     # end to end: previous order and rows from pinned host memory, the new order back
-    host_rows = [torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).pin_memory() for g in graphs]
+    if dense:
+        host_rows = [[torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).pin_memory()] for g in graphs]
+        dev_rows = [[r] for r in rows]
+    else:
+        host_rows = [[torch.from_numpy(g.row_ptr).pin_memory(), torch.from_numpy(g.col).pin_memory()] for g in graphs]
+        dev_rows = [list(r) for r in rows]
     host_prev = [p.cpu().pin_memory() for p in prev]
     host_out = [torch.empty(g.n, dtype=torch.int32).pin_memory() for g in graphs]
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, min(args.steps, 5)) if dense else 1
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for hr, dr, hp, dp in zip(host_rows, rows, host_prev, prev):
-            dr.copy_(hr, non_blocking=True)
+        for hrs, drs, hp, dp in zip(host_rows, dev_rows, host_prev, prev):
+            for hr, dr in zip(hrs, drs):
+                dr.copy_(hr, non_blocking=True)
             dp.copy_(hp, non_blocking=True)
         step()
         for ho, o in zip(host_out, orders):
@@ -588,16 +611,17 @@ def run_sweep(args):
         raise SystemExit("parity failure on the host-buffer path")
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
-    n, words = graphs[0].n, graphs[0].words
+    n = graphs[0].n
     sweep_ms = prof["lexbfs_ms"] / max(1, prof["lexbfs_launches"])
-    lex_bytes = n * words * 4
+    lex_bytes = n * graphs[0].words * 4 if dense else 8 * n + 4 * graphs[0].nnz
     line = {
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps, "warmup": warm,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 bitsets / int32 (exact)", "data": "synthetic",
         "config": dict(cfg, l2="flushed before each timed step (256 MiB write)",
                        parallelism="replicas" if world > 1 else "single GPU"),
-        "roofline": {"bound": "hbm", "kernel": "lexbfs_dense_kernel on the relabelled copy", "achieved":
+        "roofline": {"bound": "hbm", "kernel": ("lexbfs_dense_kernel" if dense else "lexbfs_csr_kernel")
+                     + " on the relabelled copy", "achieved":
                      lex_bytes / (sweep_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                      "frac": lex_bytes / (sweep_ms * 1e-3) / 1e9 / hbm, "traffic": None,
                      "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": lex_bytes},
@@ -607,14 +631,15 @@ def run_sweep(args):
         "e2e": {"value": len(graphs) * e2e_steps * world / e2e_s, "unit": "sweeps/s",
                 "h2d_bytes_per_step": sum(g.nbytes + 4 * g.n for g in graphs),
                 "d2h_bytes_per_step": sum(4 * g.n for g in graphs),
-                "path": "pinned host rows + previous order -> device, cg_lexbfs_sweep_dense (LexBFS+), order -> host"},
+                "path": "pinned host graph + previous order -> device, cg_lexbfs_sweep_%s (LexBFS+), order -> host"
+                        % ("dense" if dense else "csr")},
         "gpu_launches": int(prof["kernel_launches"]),
         "clocks": clocks,
     }
     if rank == 0 and world == 1:
         t0 = time.perf_counter()
         done = 0
-        while time.perf_counter() - t0 < 10.0:
+        while time.perf_counter() - t0 < (10.0 if dense else 4.0):
             for g, p in zip(graphs, prev_h):
                 oracle.lexbfs_plus(g, p)
                 done += 1
@@ -894,7 +919,7 @@ def main():
                     help="vertex ordering of the test (dense workloads): LexBFS (default) or MCS")
     ap.add_argument("--workload", default="dense16k",
                     choices=["dense16k", "small1k", "sparse1m", "sparse64k", "batch4096", "serve", "paper7",
-                             "sweep16k"])
+                             "sweep16k", "sweep1m"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -902,7 +927,7 @@ def main():
         return run_serve(args)
     if args.workload == "paper7":
         return run_paper7(args)
-    if args.workload == "sweep16k":
+    if args.workload in ("sweep16k", "sweep1m"):
         return run_sweep(args)
     return run_gpu(args)
 
