@@ -122,11 +122,19 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
     // the pivot's row, fetched ahead when the pivot is known early
     int64_t pbeg = row_ptr[0], pend = row_ptr[1];
     int pcol = (pend - pbeg <= 32 && pbeg + lane < pend) ? col[pbeg + lane] : -1;
+    // the pivot's class, its successor in that class and the class size, carried
+    // in registers from the step that chose the pivot (it computed them), which
+    // saves two dependent loads at the start of most steps
+    bool carry = false;
+    int cf_f = 0, cf_nx = 0, cf_size = 0;
     for (int i = 0; i < n; ++i) {
         // ---- number x (the first member of the top class f)
-        const int f = s.cls[x];
-        const int nx = s.vnext[x];
-        const int fsize = s.csize[f] - 1;
+        const int f = carry ? cf_f : s.cls[x];
+        const int nx = carry ? cf_nx : s.vnext[x];
+        const int fsize = (carry ? cf_size : s.csize[f]) - 1;
+        // x's successor's successor: the carry when that successor is the next pivot
+        const int nnx = nx != kNone ? s.vnext[nx] : kNone;
+        carry = false;
         // when f holds only x, the class after it becomes the top class
         const int g_after = nx == kNone ? s.cnext[f] : kNone;
         const int g_first = g_after != kNone ? s.cfirst[g_after] : kNone;
@@ -159,15 +167,20 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
             // next pivot: the lowest moved vertex of the top class f; else f's
             // next member; else (f emptied) the lowest moved vertex of the class
             // after f, or its first member
+            int src_lane = -1;     // lane holding the next pivot when it is a moved vertex
+            bool via_nx = false;   // the next pivot is x's successor in f (f did not split)
             {
                 const unsigned inf = __ballot_sync(kFull, valid && c0 == f);
                 if (inf) {
-                    next_x = __shfl_sync(kFull, y, __ffs(inf) - 1);
+                    src_lane = __ffs(inf) - 1;
+                    next_x = __shfl_sync(kFull, y, src_lane);
                 } else if (nx != kNone) {
                     next_x = nx;
+                    via_nx = true;
                 } else if (g_after != kNone) {
                     const unsigned ing = __ballot_sync(kFull, valid && c0 == g_after);
-                    next_x = ing ? __shfl_sync(kFull, y, __ffs(ing) - 1) : g_first;
+                    if (ing) src_lane = __ffs(ing) - 1;
+                    next_x = ing ? __shfl_sync(kFull, y, src_lane) : g_first;
                 }
                 if (next_x >= 0) {   // fetch its row now, overlapping the rest of the step
                     pbeg = row_ptr[next_x];
@@ -214,6 +227,18 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
             const int lval = __shfl_sync(kFull, op, l_lane);
             const int last_lane = valid ? highest_lane(g) : lane;
             const int last_y = __shfl_sync(kFull, y, last_lane);
+            // the next pivot's class, successor and class size after this step
+            if (src_lane >= 0) {
+                cf_f = __shfl_sync(kFull, split ? cn : c0, src_lane);
+                cf_nx = __shfl_sync(kFull, split ? ny : on, src_lane);
+                cf_size = __shfl_sync(kFull, split ? moved : csz, src_lane);
+                carry = true;
+            } else if (via_nx) {
+                cf_f = f;
+                cf_nx = nnx;
+                cf_size = fsize;
+                carry = true;
+            }
             __syncwarp();
             if (first && split) {
                 s.cnext[cpv] = cn;
