@@ -135,25 +135,29 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
         // x's successor's successor: the carry when that successor is the next pivot
         const int nnx = nx != kNone ? s.vnext[nx] : kNone;
         carry = false;
-        // when f holds only x, the class after it becomes the top class
+        // when f holds only x, the class after it becomes the top class (the load
+        // is waited for only after the neighbours' classes have been gathered)
         const int g_after = nx == kNone ? s.cnext[f] : kNone;
-        const int g_first = g_after != kNone ? s.cfirst[g_after] : kNone;
-        if (lane == 0) {
-            order[i] = x;
-            if (pos) pos[x] = i;
-            s.cls[x] = kNumberedCls;
-            s.csize[f] = fsize;
-            if (nx == kNone) {  // f held only x: drop it
-                s.cnext[HEAD] = g_after;
-                if (g_after != kNone) s.cprev[g_after] = HEAD;
-                s.freel[free_top] = f;
-            } else {
-                s.cfirst[f] = nx;
-                s.vprev[nx] = kNone;
+        // x's bookkeeping (lane 0); deferred in the single-chunk path so that it
+        // does not wait for g_after
+        auto number_x = [&]() {
+            if (lane == 0) {
+                order[i] = x;
+                if (pos) pos[x] = i;
+                s.cls[x] = kNumberedCls;
+                s.csize[f] = fsize;
+                if (nx == kNone) {  // f held only x: drop it
+                    s.cnext[HEAD] = g_after;
+                    if (g_after != kNone) s.cprev[g_after] = HEAD;
+                    s.freel[free_top - 1] = f;
+                } else {
+                    s.cfirst[f] = nx;
+                    s.vprev[nx] = kNone;
+                }
             }
-        }
-        if (nx == kNone) free_top += 1;
-        __syncwarp();
+            __syncwarp();
+        };
+        if (nx == kNone) free_top += 1;   // f goes back on the free stack
         const int64_t beg = pbeg, end = pend;
         int next_x = -1;   // set when the single-chunk path finds the next pivot itself
 
@@ -162,7 +166,15 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
             const int64_t j = beg + lane;
             const bool inrow = j < end;
             const int y = inrow ? pcol : -1;
+            // the top of the free stack, one id per lane (lane 0: f when it was just freed)
+            const int ftop = free_top - 1 - lane;
+            int fl = ftop >= 0 ? s.freel[ftop] : 0;
+            if (lane == 0 && nx == kNone) fl = f;
             const int c0 = inrow ? s.cls[y] : kNumberedCls;
+            // the list links, gathered with the classes (x's successor loses x as predecessor)
+            int op = inrow ? s.vprev[y] : 0;
+            const int on = inrow ? s.vnext[y] : 0;
+            if (y == nx) op = kNone;
             const bool valid = inrow && c0 != kNumberedCls;
             // next pivot: the lowest moved vertex of the top class f; else f's
             // next member; else (f emptied) the lowest moved vertex of the class
@@ -180,7 +192,7 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
                 } else if (g_after != kNone) {
                     const unsigned ing = __ballot_sync(kFull, valid && c0 == g_after);
                     if (ing) src_lane = __ffs(ing) - 1;
-                    next_x = ing ? __shfl_sync(kFull, y, src_lane) : g_first;
+                    next_x = ing ? __shfl_sync(kFull, y, src_lane) : s.cfirst[g_after];
                 }
                 if (next_x >= 0) {   // fetch its row now, overlapping the rest of the step
                     pbeg = row_ptr[next_x];
@@ -188,10 +200,9 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
                     pcol = (pend - pbeg <= 32 && pbeg + lane < pend) ? col[pbeg + lane] : -1;
                 }
             }
-            int op = 0, on = 0, csz = 0, cpv = 0;
+            number_x();
+            int csz = 0, cpv = 0;
             if (valid) {
-                op = s.vprev[y];
-                on = s.vnext[y];
                 csz = s.csize[c0];
                 cpv = s.cprev[c0];
                 if (parent) parent[y] = x;
@@ -205,8 +216,8 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
             // allocate one id per split class (its first member's lane)
             const unsigned need = __ballot_sync(kFull, first && split);
             const int rank = __popc(need & lanemask_lt());
-            int cn = 0;
-            if (first && split) cn = s.freel[free_top - 1 - rank];
+            int cn = __shfl_sync(kFull, fl, rank & 31);
+            if (!(first && split)) cn = 0;
             free_top -= __popc(need);
             // every member learns its class's new id from the first member
             const int src = valid ? (__ffs(g) - 1) : lane;
@@ -262,6 +273,7 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
             }
             (void)vmask;
         } else {
+            number_x();
             // ---- long row: four passes over 32-wide chunks with per-class carries
             // pass A: compact the unnumbered neighbours, save old links, count per class
             int k = 0;
