@@ -20,9 +20,13 @@
 //     (a run ends where a member's old successor is not the next moved member
 //     of the same class), linking the run's outer neighbours directly;
 //   * a class that moves entirely keeps its id, list and place;
-//   * rows longer than 32 neighbours use per-class carries (counts, next/prev
-//     member, open run) stamped with the step number, in four passes; rows of
-//     at most 32 neighbours take a register-only single pass.
+//   * rows of at most 32 neighbours take a register-only single pass by one
+//     warp; a longer row is handled by the whole CTA (the other warps wait at
+//     a named barrier during the short steps): its unnumbered neighbours are
+//     sorted by (class, row position), so that each class's moved members are
+//     adjacent and in id order, then every member links to its neighbours in
+//     the sorted array, a block-wide max-scan finds the start of each run of
+//     list-consecutive moved members, and the run ends unlink the runs.
 // parent[y] = x is recorded for every moved y: the last pivot that moves y is
 // p(y) of the perfect-elimination check (Section 5.2).
 #include <algorithm>
@@ -41,39 +45,46 @@ struct CsrState {
     int *cls, *vnext, *vprev;               // [n]
     int *cnext, *cprev;                     // [n + 1], index n = head sentinel
     int *cfirst, *clast, *csize;            // [n]
-    int *cmoved, *cstamp;                   // [n]  moved count of the step in cstamp
-    int *cfirst_idx, *clast_idx, *cchild;   // [n]  per-step carries
-    int *cprev_y, *crun_l;                  // [n]
+    int *cmoved, *cchild;                   // [n]  long-row step: moved count, new id (0 / kNone between steps)
     int *freel;                             // [n]
-    int *sy, *sc, *sop, *son, *snext;       // [max_deg] per-step neighbour scratch
+    int *sy, *sop, *son, *srun;             // [max_deg] long-row scratch by row position / sorted index
+    unsigned long long *skey;               // [next pow2 >= max_deg] (class << 32 | row position) keys
 };
 
-constexpr int kCsrArrays = 16;
+constexpr int kCsrArrays = 11;
+constexpr int kCsrThreads = 1024;      // the CTA of the search: warp 0 walks the steps
+constexpr int kSortSmem = 4096;        // keys sorted in shared memory up to this many
+
+__host__ __device__ inline int64_t pow2_at_least(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
 
 __device__ inline CsrState csr_state_carve(int *base, int64_t n, int64_t max_deg) {
     CsrState s;
     int *p = base;
     const int64_t stride = ((n + 1 + 31) / 32) * 32;
-    int **arrs[kCsrArrays] = {&s.cls,    &s.vnext,     &s.vprev,     &s.cnext,  &s.cprev,   &s.cfirst,
-                              &s.clast,  &s.csize,     &s.cmoved,    &s.cstamp, &s.cfirst_idx, &s.clast_idx,
-                              &s.cchild, &s.cprev_y,   &s.crun_l,    &s.freel};
+    int **arrs[kCsrArrays] = {&s.cls,   &s.vnext,  &s.vprev,  &s.cnext,  &s.cprev, &s.cfirst,
+                              &s.clast, &s.csize,  &s.cmoved, &s.cchild, &s.freel};
     for (int a = 0; a < kCsrArrays; ++a) {
         *arrs[a] = p;
         p += stride;
     }
     const int64_t ds = (((max_deg > 1 ? max_deg : 1) + 31) / 32) * 32;
     s.sy = p; p += ds;
-    s.sc = p; p += ds;
     s.sop = p; p += ds;
     s.son = p; p += ds;
-    s.snext = p;
+    s.srun = p; p += ds;
+    s.skey = reinterpret_cast<unsigned long long *>(p);   // p stays 8-byte aligned: every block is 32 ints
     return s;
 }
 
 __host__ inline size_t csr_state_stride_bytes(int64_t n, int64_t max_deg) {
     const int64_t stride = ((n + 1 + 31) / 32) * 32;
     const int64_t ds = ((std::max<int64_t>(max_deg, 1) + 31) / 32) * 32;
-    return (size_t)(kCsrArrays * stride + 5 * ds) * sizeof(int);
+    return (size_t)(kCsrArrays * stride + 4 * ds) * sizeof(int) +
+           (size_t)pow2_at_least(std::max<int64_t>(max_deg, 1)) * sizeof(unsigned long long);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -95,7 +106,8 @@ __global__ void csr_init_kernel(int *ws, int64_t n, int64_t max_deg, int32_t *pa
         s.cls[v] = 0;
         s.vnext[v] = v + 1 < n ? (int)(v + 1) : kNone;
         s.vprev[v] = (int)v - 1;
-        s.cstamp[v] = -1;
+        s.cmoved[v] = 0;
+        s.cchild[v] = kNone;
         s.freel[v] = (int)(v + 1);   // entries 0..n-2 used: ids 1..n-1
         if (parent) parent[v] = -1;
         if (v == 0) {
@@ -109,12 +121,231 @@ __global__ void csr_init_kernel(int *ws, int64_t n, int64_t max_deg, int32_t *pa
     }
 }
 
-// One warp walks all n steps.
-__global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t max_deg,
-                                                        const int64_t *__restrict__ row_ptr,
-                                                        const int32_t *__restrict__ col, int32_t *__restrict__ order,
-                                                        int32_t *__restrict__ pos, int32_t *__restrict__ parent) {
+// Shared parameters of a long-row step.
+struct LongShared {
+    int64_t beg, end;
+    int x, free_top, nvalid, done;
+    int carry;            // run-start scan carry
+    int wmax[32];         // per-warp maxima of the scan
+};
+
+__device__ __forceinline__ void bar_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kCsrThreads) : "memory");
+}
+
+// Sorts key[0..p) ascending (p a power of two), all threads of the CTA.
+__device__ void cta_sort_keys(unsigned long long *key, int64_t p) {
+    for (int64_t k = 2; k <= p; k <<= 1) {
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            for (int64_t i = threadIdx.x; i < p; i += blockDim.x) {
+                const int64_t l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = key[i], b = key[l];
+                    if ((a > b) == ((i & k) == 0)) {
+                        key[i] = b;
+                        key[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// The same network for p > kSortSmem keys in global memory: the passes with
+// a stride below kSortSmem pair keys inside one aligned tile of kSortSmem
+// keys, so they run on a shared-memory copy of each tile (the first log2 of
+// them for every k up to the tile size, the rest after each k's global passes).
+__device__ void cta_sort_keys_tiled(unsigned long long *key, int64_t p, unsigned long long *tile) {
+    const int T = blockDim.x;
+    auto tile_passes = [&](int64_t t0, int64_t k_lo, int64_t k_hi, int64_t j_first) {
+        for (int li = threadIdx.x; li < kSortSmem; li += T) tile[li] = key[t0 + li];
+        __syncthreads();
+        for (int64_t k = k_lo; k <= k_hi; k <<= 1) {
+            for (int64_t j = (k == k_lo ? j_first : (k >> 1)); j > 0; j >>= 1) {
+                for (int li = threadIdx.x; li < kSortSmem; li += T) {
+                    const int l = li ^ (int)j;
+                    if (l > li) {
+                        const unsigned long long a = tile[li], b = tile[l];
+                        if ((a > b) == (((t0 + li) & k) == 0)) {
+                            tile[li] = b;
+                            tile[l] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int li = threadIdx.x; li < kSortSmem; li += T) key[t0 + li] = tile[li];
+        __syncthreads();
+    };
+    for (int64_t t0 = 0; t0 < p; t0 += kSortSmem) tile_passes(t0, 2, kSortSmem, 1);   // k = 2 .. tile size
+    for (int64_t k = 2 * kSortSmem; k <= p; k <<= 1) {
+        for (int64_t j = k >> 1; j >= kSortSmem; j >>= 1) {
+            for (int64_t i = threadIdx.x; i < p; i += T) {
+                const int64_t l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = key[i], b = key[l];
+                    if ((a > b) == ((i & k) == 0)) {
+                        key[i] = b;
+                        key[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        for (int64_t t0 = 0; t0 < p; t0 += kSortSmem) tile_passes(t0, k, k, kSortSmem >> 1);
+    }
+}
+
+// One long-row step for pivot sh->x (row [sh->beg, sh->end)), the whole CTA;
+// x's own bookkeeping is done.  The unnumbered neighbours, keyed by (class,
+// row position) and sorted, put each class's moved members next to each other
+// in id order (rows are sorted); the first key of a class decides the split
+// (moved < size: a new class from the free stack, linked before it), every
+// moved member links to its sorted neighbours of the same class, a max-scan of
+// run starts (a member whose predecessor in the old list is not the previous
+// moved member) gives each run end the run's outer left neighbour, and the run
+// ends unlink the runs from the old list.  cmoved / cchild return to 0 / kNone.
+__device__ void long_row_step(const CsrState &s, const int32_t *__restrict__ col, int32_t *__restrict__ parent,
+                              LongShared *sh) {
+    __shared__ unsigned long long skeys[kSortSmem];
+    const int t = threadIdx.x, T = blockDim.x;
+    const int x = sh->x;
+    const int64_t beg = sh->beg;
+    const int d = (int)(sh->end - beg);
+    const int64_t p = pow2_at_least(d);
+    unsigned long long *key = p <= kSortSmem ? skeys : s.skey;
+    constexpr unsigned long long kInf = ~0ull;
+    for (int64_t k = t; k < p; k += T) {
+        unsigned long long e = kInf;
+        if (k < d) {
+            const int y = col[beg + k];
+            const int c = s.cls[y];
+            if (c != kNumberedCls) {
+                e = ((unsigned long long)(unsigned)c << 32) | (unsigned)k;
+                s.sy[k] = y;
+                s.sop[k] = s.vprev[y];
+                s.son[k] = s.vnext[y];
+                atomicAdd(&s.cmoved[c], 1);
+                atomicAdd(&sh->nvalid, 1);
+                if (parent) parent[y] = x;
+            }
+        }
+        key[k] = e;
+    }
+    __syncthreads();
+    if (p <= kSortSmem) cta_sort_keys(key, p);
+    else cta_sort_keys_tiled(key, p, skeys);
+    const int K = sh->nvalid;
+    auto cls_of = [&](int k) { return (int)(key[k] >> 32); };
+    auto pos_of = [&](int k) { return (int)(key[k] & 0xFFFFFFFFu); };
+    // class firsts: split decision, new id, insertion before the old class
+    for (int k = t; k < K; k += T) {
+        const int c = cls_of(k);
+        if (k > 0 && cls_of(k - 1) == c) continue;
+        const int m = s.cmoved[c], sz = s.csize[c];
+        if (m < sz) {
+            const int cn = s.freel[atomicSub(&sh->free_top, 1) - 1];
+            s.cchild[c] = cn;
+            const int pc = s.cprev[c];
+            s.cnext[pc] = cn;
+            s.cprev[cn] = pc;
+            s.cnext[cn] = c;
+            s.cprev[c] = cn;
+            s.cfirst[cn] = s.sy[pos_of(k)];
+            s.csize[cn] = m;
+            s.csize[c] = sz - m;
+        }
+    }
+    __syncthreads();
+    // run starts and their max-scan over the sorted array (runs never cross classes)
+    if (t == 0) sh->carry = -1;
+    __syncthreads();
+    for (int base = 0; base < K; base += T) {
+        const int k = base + t;
+        int v = -1;
+        if (k < K) {
+            const int c = cls_of(k);
+            if (s.cchild[c] != kNone) {
+                const int py = (k > 0 && cls_of(k - 1) == c) ? s.sy[pos_of(k - 1)] : kNone;
+                if (py == kNone || s.sop[pos_of(k)] != py) v = k;
+            }
+        }
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if ((t & 31) >= o) incl = max(incl, y);
+        }
+        if ((t & 31) == 31) sh->wmax[t >> 5] = incl;
+        __syncthreads();
+        int before = sh->carry;
+        for (int w = 0; w < (t >> 5); ++w) before = max(before, sh->wmax[w]);
+        if (k < K) s.srun[k] = max(before, incl);
+        __syncthreads();
+        if (t == 0) {
+            int m = sh->carry;
+            for (int w = 0; w < (T >> 5); ++w) m = max(m, sh->wmax[w]);
+            sh->carry = m;
+        }
+        __syncthreads();
+    }
+    // links of the moved members, the new lists' last members, the runs unlinked
+    for (int k = t; k < K; k += T) {
+        const int c = cls_of(k);
+        const int cn = s.cchild[c];
+        if (cn == kNone) continue;
+        const int j = pos_of(k);
+        const int y = s.sy[j];
+        const bool has_prev = k > 0 && cls_of(k - 1) == c;
+        const bool has_next = k + 1 < K && cls_of(k + 1) == c;
+        const int py = has_prev ? s.sy[pos_of(k - 1)] : kNone;
+        const int ny = has_next ? s.sy[pos_of(k + 1)] : kNone;
+        const int on = s.son[j];
+        s.vprev[y] = py;
+        s.vnext[y] = ny;
+        s.cls[y] = cn;
+        if (!has_next) s.clast[cn] = y;
+        if (ny == kNone || on != ny) {   // run end: link the run's outer neighbours
+            const int L = s.sop[pos_of(s.srun[k])], R = on;
+            if (L == kNone) s.cfirst[c] = R; else s.vnext[L] = R;
+            if (R == kNone) s.clast[c] = L; else s.vprev[R] = L;
+        }
+    }
+    __syncthreads();
+    for (int k = t; k < K; k += T) {   // per-class step state back to its resting values
+        const int c = cls_of(k);
+        if (k > 0 && cls_of(k - 1) == c) continue;
+        s.cmoved[c] = 0;
+        s.cchild[c] = kNone;
+    }
+    if (t == 0) sh->nvalid = 0;
+    __syncthreads();
+}
+
+// One warp walks all n steps; the other warps of the CTA join the long-row steps.
+
+__global__ void __launch_bounds__(kCsrThreads) lexbfs_csr_kernel(int *ws, int n, int64_t max_deg,
+                                                                 const int64_t *__restrict__ row_ptr,
+                                                                 const int32_t *__restrict__ col,
+                                                                 int32_t *__restrict__ order, int32_t *__restrict__ pos,
+                                                                 int32_t *__restrict__ parent) {
     CsrState s = csr_state_carve(ws, n, max_deg);
+    __shared__ LongShared shs;
+    LongShared *sh = &shs;
+    if (threadIdx.x == 0) {
+        sh->done = 0;
+        sh->nvalid = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) {   // helper warps: join the long-row steps, then leave when warp 0 is done
+        for (;;) {
+            bar_sync(1);
+            if (sh->done) return;
+            long_row_step(s, col, parent, sh);
+        }
+    }
     const int lane = threadIdx.x;
     const int HEAD = n;
     int free_top = n - 1;
@@ -274,140 +505,17 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
             (void)vmask;
         } else {
             number_x();
-            // ---- long row: four passes over 32-wide chunks with per-class carries
-            // pass A: compact the unnumbered neighbours, save old links, count per class
-            int k = 0;
-            for (int64_t base = beg; base < end; base += 32) {
-                const int64_t j = base + lane;
-                const bool inrow = j < end;
-                const int y = inrow ? col[j] : -1;
-                const int c = inrow ? s.cls[y] : kNumberedCls;
-                const bool valid = inrow && c != kNumberedCls;
-                const unsigned m = __ballot_sync(kFull, valid);
-                const int idx = k + __popc(m & lanemask_lt());
-                const unsigned grp = __match_any_sync(kFull, valid ? c : kNumberedCls);
-                if (valid) {
-                    s.sy[idx] = y;
-                    s.sc[idx] = c;
-                    s.sop[idx] = s.vprev[y];
-                    s.son[idx] = s.vnext[y];
-                    if (parent) parent[y] = x;
-                    if ((grp & lanemask_lt()) == 0) {  // group leader
-                        const int cnt = __popc(grp);
-                        if (s.cstamp[c] != i) {
-                            s.cstamp[c] = i;
-                            s.cmoved[c] = cnt;
-                            s.cfirst_idx[c] = kNone;
-                            s.cchild[c] = kNone;
-                            s.cprev_y[c] = kNone;
-                            s.crun_l[c] = kNone;
-                        } else {
-                            s.cmoved[c] += cnt;
-                        }
-                    }
-                }
-                k += __popc(m);
-                __syncwarp();
+            // ---- long row: the whole CTA (the other warps wait at barrier 1)
+            if (lane == 0) {
+                sh->x = x;
+                sh->beg = beg;
+                sh->end = end;
+                sh->free_top = free_top;
             }
-            const int nchunks = (k + 31) / 32;
-            // pass B (reverse): next member index of the same class; first / last index per class
-            for (int ch = nchunks - 1; ch >= 0; --ch) {
-                const int idx = ch * 32 + lane;
-                const bool valid = idx < k;
-                const int c = valid ? s.sc[idx] : kNumberedCls;
-                const unsigned grp = __match_any_sync(kFull, valid ? c : kNumberedCls);
-                const unsigned g = valid ? grp : 0u;
-                const unsigned higher = g & lanemask_gt();
-                int carry = kNone;
-                if (valid && !higher) carry = s.cfirst_idx[c];   // the class's lowest index in later chunks
-                __syncwarp();
-                if (valid) {
-                    s.snext[idx] = higher ? ch * 32 + (__ffs(higher) - 1) : carry;
-                    if (!higher && carry == kNone) s.clast_idx[c] = idx;   // last member of the class
-                    if ((g & lanemask_lt()) == 0) s.cfirst_idx[c] = idx;
-                }
-                __syncwarp();
-            }
-            // pass C: one allocation per split class, at its first member
-            for (int ch = 0; ch < nchunks; ++ch) {
-                const int idx = ch * 32 + lane;
-                const bool valid = idx < k;
-                const int c = valid ? s.sc[idx] : 0;
-                const bool first = valid && s.cfirst_idx[c] == idx;
-                int moved = 0, size = 0;
-                if (first) {
-                    moved = s.cmoved[c];
-                    size = s.csize[c];
-                }
-                const bool split = first && moved < size;
-                const unsigned need = __ballot_sync(kFull, split);
-                const int rank = __popc(need & lanemask_lt());
-                if (split) {
-                    const int cn = s.freel[free_top - 1 - rank];
-                    const int p = s.cprev[c];
-                    s.cnext[p] = cn;
-                    s.cprev[cn] = p;
-                    s.cnext[cn] = c;
-                    s.cprev[c] = cn;
-                    s.cfirst[cn] = s.sy[idx];
-                    s.clast[cn] = s.sy[s.clast_idx[c]];
-                    s.csize[cn] = moved;
-                    s.csize[c] = size - moved;
-                    s.cchild[c] = cn;
-                }
-                free_top -= __popc(need);
-                __syncwarp();
-            }
-            // pass D: unlink moved runs from the old lists, link the new lists
-            for (int ch = 0; ch < nchunks; ++ch) {
-                const int idx = ch * 32 + lane;
-                const bool inr = idx < k;
-                const int c = inr ? s.sc[idx] : kNumberedCls;
-                const int cn = inr ? s.cchild[c] : kNone;
-                const bool split = inr && cn != kNone;
-                const unsigned grp = __match_any_sync(kFull, split ? c : kNumberedCls);
-                const unsigned g = split ? grp : 0u;
-                int y = 0, op = 0, on = 0, ny = kNone, carry_py = kNone, carry_l = kNone;
-                if (split) {
-                    y = s.sy[idx];
-                    op = s.sop[idx];
-                    on = s.son[idx];
-                    const int nidx = s.snext[idx];
-                    ny = nidx >= 0 ? s.sy[nidx] : kNone;
-                    if ((g & lanemask_lt()) == 0) {
-                        carry_py = s.cprev_y[c];
-                        carry_l = s.crun_l[c];
-                    }
-                }
-                const unsigned lower = g & lanemask_lt();
-                const int lead = split ? (__ffs(g) - 1) : lane;
-                carry_py = __shfl_sync(kFull, carry_py, lead);
-                carry_l = __shfl_sync(kFull, carry_l, lead);
-                const int py_v = __shfl_sync(kFull, y, lower ? highest_lane(lower) : lane);
-                const int py = lower ? py_v : carry_py;
-                const bool is_start = split && (py == kNone || op != py);
-                const bool is_end = split && (ny == kNone || on != ny);
-                const unsigned starts = __ballot_sync(kFull, is_start);
-                const unsigned s_le = g & starts & (lanemask_lt() | (1u << lane));
-                const int lv = __shfl_sync(kFull, op, s_le ? highest_lane(s_le) : lane);
-                const int lval = s_le ? lv : carry_l;
-                __syncwarp();
-                if (is_end) {
-                    const int L = lval, R = on;
-                    if (L == kNone) s.cfirst[c] = R; else s.vnext[L] = R;
-                    if (R == kNone) s.clast[c] = L; else s.vprev[R] = L;
-                }
-                if (split) {
-                    s.vprev[y] = py;
-                    s.vnext[y] = ny;
-                    s.cls[y] = cn;
-                    if (lane == highest_lane(g)) {   // carries for the next chunk
-                        s.cprev_y[c] = y;
-                        s.crun_l[c] = lval;
-                    }
-                }
-                __syncwarp();
-            }
+            __syncwarp();
+            bar_sync(1);
+            long_row_step(s, col, parent, sh);
+            free_top = sh->free_top;
         }
         __syncwarp();
         // ---- next pivot: first member of the top class
@@ -422,6 +530,9 @@ __global__ void __launch_bounds__(32) lexbfs_csr_kernel(int *ws, int n, int64_t 
             x = next_x;
         }
     }
+    if (lane == 0) sh->done = 1;
+    __syncwarp();
+    bar_sync(1);
 }
 
 }  // namespace
@@ -434,7 +545,8 @@ int lexbfs_csr_launch(int n, int64_t max_deg, const int64_t *row_ptr, const int3
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms * 4));
     csr_init_kernel<<<blocks, 256, 0, stream>>>(static_cast<int *>(ws), n, max_deg, parent);
     CG_LAUNCH_CHECK("csr_init_kernel");
-    lexbfs_csr_kernel<<<1, 32, 0, stream>>>(static_cast<int *>(ws), n, max_deg, row_ptr, col, order, pos, parent);
+    lexbfs_csr_kernel<<<1, kCsrThreads, 0, stream>>>(static_cast<int *>(ws), n, max_deg, row_ptr, col, order, pos,
+                                                     parent);
     CG_LAUNCH_CHECK("lexbfs_csr_kernel");
     return CG_OK;
 }
