@@ -81,6 +81,26 @@ def test_long_rows_multi_chunk(ctx):
     assert assert_parity(ctx, gg.dense_to_csr(h)).chordal == 0
 
 
+@pytest.mark.parametrize("leaves", [32, 33, 4095, 4096, 4097, 9000])
+def test_long_row_sort_sizes(ctx, leaves):
+    """A hub row at the boundaries of the long-row step: 32 neighbours (one
+    warp), 33 (the CTA), 4,096 keys (the last shared-memory sort) and longer
+    rows (the tiled sort on the workspace), with a few extra edges among the
+    leaves so that the hub's neighbours fall into several classes."""
+    n = leaves + 1
+    eu, ev = [0] * leaves, list(range(1, n))
+    rng = np.random.Generator(np.random.PCG64(leaves))
+    for _ in range(leaves // 3):
+        a, b = sorted(rng.choice(np.arange(1, n), 2, replace=False).tolist())
+        eu.append(a)
+        ev.append(b)
+    g = gg.csr_from_edges(n, np.array(eu, np.int64), np.array(ev, np.int64))
+    assert_parity(ctx, g)
+    # the same hub numbered late: its row is long when most of it is unnumbered
+    perm = rng.permutation(n)
+    assert_parity(ctx, gg.relabel_csr(g, perm))
+
+
 @pytest.mark.parametrize("n", [10, 1000, 20000, 200000])
 def test_peo_construction(ctx, n):
     g = gg.peo_csr(n, n + 1)
