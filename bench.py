@@ -857,6 +857,7 @@ def run_gpu(args):
         phases.update({"lexbfs_ms_per_launch": lex_ms, "check_ms_per_launch": chk_ms,
                        "lexbfs_ns_per_step": lex_ms * 1e6 / graphs[0].n, "check_gbs": chk_gbs,
                        "check_frac_of_hbm": chk_gbs / hbm})
+        phases["floor"] = step_floor(all_ctx[0], stream, phases["lexbfs_ns_per_step"])
     else:
         run_ms = prof["batch_ms"] / max(1, prof["batch_calls"])
         gbs = alg / (run_ms * 1e-3) / 1e9
@@ -912,6 +913,20 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def step_floor(ctx, stream, ns_per_step: float) -> dict:
+    """Latency floors of one sequential step, measured after the timed region:
+    a pair of CTA barriers (1,024 threads), one dependent load over a 32 MiB
+    chain (L2-resident, like the 32 MiB dense graph) and over a 1 GiB chain
+    (mostly DRAM)."""
+    from paper_1508_06329_gb300 import binding as B
+    l2 = B.step_floor(ctx, threads=1024, iters=16384, chain_bytes=32 << 20, loads=100000, stream=stream)
+    dram = B.step_floor(ctx, threads=1024, iters=1024, chain_bytes=1 << 30, loads=20000, stream=stream)
+    floor = l2["barrier_pair_ns"] + l2["load_ns"]
+    return {"barrier_pair_ns": l2["barrier_pair_ns"], "l2_load_ns": l2["load_ns"], "dram_load_ns": dram["load_ns"],
+            "barrier_pair_plus_l2_load_ns": floor, "step_over_that": ns_per_step / floor,
+            "step_in_l2_loads": ns_per_step / l2["load_ns"]}
 
 
 def main():

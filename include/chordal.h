@@ -338,6 +338,30 @@ int cg_autotune_get(cg_context *ctx, int32_t *threads, int32_t slots);
 int cg_autotune_set(cg_context *ctx, const int32_t *threads, int32_t slots);
 int cg_profile_read(cg_context *ctx, cg_profile *out);
 
+/*
+ * Latency floors of one step of the sequential LexBFS loop (measurement aid,
+ * not part of the paper; Section 6.1 runs n dependent steps, so a step's
+ * fixed costs bound the whole order).  Synchronises `stream`; allocates and
+ * frees its own scratch.
+ *   threads      CTA size of the barrier loop, a multiple of 32 in [32, 1024]
+ *   iters        barrier-loop iterations, [1, 2^24]; each is two CTA-wide
+ *                barriers, the dense step's fixed synchronisation
+ *   chain_bytes  footprint of the load chain, [256, 2^32] bytes (rounded down
+ *                to a power of two of 128-byte lines): one node per line, in
+ *                a scattered single cycle; within L2 (129 MB) every load is an
+ *                L2 round trip, far above it mostly a DRAM round trip
+ *   loads        dependent loads one thread follows, [1, 2^24]
+ * Each time is the best of three, minus the same launch with no work.
+ * CG_EINVAL on an argument out of range, CG_ENOMEM / CG_ECUDA otherwise.
+ */
+typedef struct {
+    double barrier_pair_ns;  /* one iteration of two CTA-wide barriers */
+    double load_ns;          /* one dependent load (L1 bypassed) */
+    int64_t chain_bytes;     /* the chain's footprint after rounding */
+} cg_step_floor_info;
+int cg_step_floor(cg_context *ctx, int32_t threads, int32_t iters, int64_t chain_bytes, int32_t loads,
+                  cudaStream_t stream, cg_step_floor_info *out);
+
 #ifdef __cplusplus
 }
 #endif

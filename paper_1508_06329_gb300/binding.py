@@ -57,6 +57,10 @@ class cg_queue_config(ctypes.Structure):
                 ("max_batch", ctypes.c_int32), ("max_pending", ctypes.c_int32), ("max_batch_large", ctypes.c_int32)]
 
 
+class cg_step_floor_info(ctypes.Structure):
+    _fields_ = [("barrier_pair_ns", ctypes.c_double), ("load_ns", ctypes.c_double), ("chain_bytes", ctypes.c_int64)]
+
+
 class cg_queue_info(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "pending", "inflight", "batches",
                                               "pool_free_bytes")]
@@ -108,6 +112,7 @@ SIGNATURES = {
     "cg_autotune_get": ([P, P, I32], ctypes.c_int),
     "cg_autotune_set": ([P, P, I32], ctypes.c_int),
     "cg_profile_read": ([P, P], ctypes.c_int),
+    "cg_step_floor": ([P, I32, I32, I64, I32, P, P], ctypes.c_int),
 }
 
 _lock = threading.Lock()
@@ -177,6 +182,7 @@ cg_batch_autotune = _fn("cg_batch_autotune")
 cg_autotune_get = _fn("cg_autotune_get")
 cg_autotune_set = _fn("cg_autotune_set")
 cg_profile_read = _fn("cg_profile_read")
+cg_step_floor = _fn("cg_step_floor")
 
 
 # --------------------------------------------------------------------------- torch-facing helpers
@@ -404,6 +410,15 @@ def autotune_get(ctx: Context) -> list:
 def autotune_set(ctx: Context, table) -> None:
     buf = (ctypes.c_int32 * 9)(*[int(x) for x in table][:9])
     _check(cg_autotune_set(ctx.handle, buf, 9))
+
+
+def step_floor(ctx: Context, threads: int = 1024, iters: int = 16384, chain_bytes: int = 32 << 20,
+               loads: int = 100000, stream=None) -> dict:
+    """Latency floors of one LexBFS step (cg_step_floor): ns per pair of CTA
+    barriers and ns per dependent load over a chain of `chain_bytes`."""
+    out = cg_step_floor_info()
+    _check(cg_step_floor(ctx.handle, threads, iters, chain_bytes, loads, _stream(stream), ctypes.byref(out)))
+    return {f: getattr(out, f) for f, _ in cg_step_floor_info._fields_}
 
 
 class Queue:

@@ -398,7 +398,7 @@ int run_single_csr(cg_context *ctx, const cg_csr *g, int32_t *order_out, int32_t
     int32_t *parent = at<int32_t>(ctx, o_parent);
     if (n > 0) {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
-        if ((rc = lexbfs_csr_launch(n, n, g->row_ptr, g->col, order, pos, parent, at<void>(ctx, o_state),
+        if ((rc = lexbfs_csr_launch(n, n, g->row_ptr, g->col, g->nnz, order, pos, parent, at<void>(ctx, o_state),
                                     ctx->num_sms, stream)))
             return rc;
         ctx->launches += 2;
@@ -579,7 +579,7 @@ int cg_lexbfs_sweep_csr(cg_context *ctx, const cg_csr *g, int32_t kind, const in
     if ((rc = sweep_csr_relabel_launch(n, g->nnz, g->row_ptr, g->col, sb, at<void>(ctx, o_relabel), &rp_new,
                                        &col_new, ctx->num_sms, stream)))
         return rc;
-    if ((rc = lexbfs_csr_launch(n, n, rp_new, col_new, sb.order_p, sb.pos_p, nullptr, at<void>(ctx, o_state),
+    if ((rc = lexbfs_csr_launch(n, n, rp_new, col_new, g->nnz, sb.order_p, sb.pos_p, nullptr, at<void>(ctx, o_state),
                                 ctx->num_sms, stream)))
         return rc;
     if ((rc = sweep_unpermute_launch(n, sb, order, pos, ctx->num_sms, stream))) return rc;

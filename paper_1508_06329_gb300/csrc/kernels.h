@@ -102,9 +102,9 @@ int sweep_order_launch(const DenseDesc &d, const LexPlan &plan, void *gstate, in
 int mcs_dense_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, int ctas, int32_t *order,
                      int32_t *pos, int *work_counter, cudaStream_t stream);
 
-// ---- CSR LexBFS (lexbfs_csr.cu): one warp per graph, state in `ws`
+// ---- CSR LexBFS (lexbfs_csr.cu): one CTA per graph (warp 0 walks the steps), state in `ws`
 size_t lexbfs_csr_workspace_bytes(int64_t n, int64_t max_deg);
-int lexbfs_csr_launch(int n, int64_t max_deg, const int64_t *row_ptr, const int32_t *col, int32_t *order,
+int lexbfs_csr_launch(int n, int64_t max_deg, const int64_t *row_ptr, const int32_t *col, int64_t nnz, int32_t *order,
                       int32_t *pos, int32_t *parent, void *ws, int num_sms, cudaStream_t stream);
 
 // ---- CSR check (peo_csr.cu)

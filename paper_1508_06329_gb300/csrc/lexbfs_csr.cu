@@ -5,8 +5,9 @@
 // class C by C ∩ N_x placed before C \ N_x.  Its O(N + M) form keeps each
 // class as a list sorted by vertex id and moves only the neighbours of x.
 //
-// GPU form (one warp per graph; the state of n vertices lives in a global
-// workspace and stays L2-resident):
+// GPU form (one CTA per graph, whose warp 0 walks the steps; the state of n
+// vertices lives in a global workspace and stays L2-resident, and the graph
+// is bulk-prefetched into L2 at launch):
 //   * cls[v], and per class a doubly linked member list sorted by id
 //     (vnext/vprev, cfirst/clast), its size, and the class list
 //     (cnext/cprev, head sentinel n) ordered top first; a free stack of ids;
@@ -328,7 +329,7 @@ __device__ void long_row_step(const CsrState &s, const int32_t *__restrict__ col
 
 __global__ void __launch_bounds__(kCsrThreads) lexbfs_csr_kernel(int *ws, int n, int64_t max_deg,
                                                                  const int64_t *__restrict__ row_ptr,
-                                                                 const int32_t *__restrict__ col,
+                                                                 const int32_t *__restrict__ col, int64_t nnz,
                                                                  int32_t *__restrict__ order, int32_t *__restrict__ pos,
                                                                  int32_t *__restrict__ parent) {
     CsrState s = csr_state_carve(ws, n, max_deg);
@@ -338,6 +339,11 @@ __global__ void __launch_bounds__(kCsrThreads) lexbfs_csr_kernel(int *ws, int n,
         sh->done = 0;
         sh->nvalid = 0;
     }
+    // Every row is read once, when its vertex is the pivot, so its first read
+    // would be a DRAM miss on the step's dependent chain: pull row_ptr and col
+    // into L2 (bulk prefetch, no completion wait) while the search starts.
+    prefetch_range_l2<kCsrThreads>(row_ptr, (size_t)(n + 1) * sizeof(int64_t));
+    prefetch_range_l2<kCsrThreads>(col, (size_t)nnz * sizeof(int32_t));
     __syncthreads();
     if (threadIdx.x >= 32) {   // helper warps: join the long-row steps, then leave when warp 0 is done
         for (;;) {
@@ -358,6 +364,11 @@ __global__ void __launch_bounds__(kCsrThreads) lexbfs_csr_kernel(int *ws, int n,
     // saves two dependent loads at the start of most steps
     bool carry = false;
     int cf_f = 0, cf_nx = 0, cf_size = 0;
+    // the class after the pivot's class, carried when that class holds only
+    // the pivot (the common case on sparse graphs): the step that chose the
+    // pivot read it and corrected it for its own splits
+    bool ga_known = false;
+    int ga = kNone;
     for (int i = 0; i < n; ++i) {
         // ---- number x (the first member of the top class f)
         const int f = carry ? cf_f : s.cls[x];
@@ -368,7 +379,11 @@ __global__ void __launch_bounds__(kCsrThreads) lexbfs_csr_kernel(int *ws, int n,
         carry = false;
         // when f holds only x, the class after it becomes the top class (the load
         // is waited for only after the neighbours' classes have been gathered)
-        const int g_after = nx == kNone ? s.cnext[f] : kNone;
+        const int g_after = nx == kNone ? (ga_known ? ga : s.cnext[f]) : kNone;
+        ga_known = false;
+        // that class's first member, read ahead: when x has no neighbour in
+        // it, it is the next pivot (and the class is untouched by this step)
+        const int d_first = g_after != kNone ? s.cfirst[g_after] : kNone;
         // x's bookkeeping (lane 0); deferred in the single-chunk path so that it
         // does not wait for g_after
         auto number_x = [&]() {
@@ -407,11 +422,22 @@ __global__ void __launch_bounds__(kCsrThreads) lexbfs_csr_kernel(int *ws, int n,
             const int on = inrow ? s.vnext[y] : 0;
             if (y == nx) op = kNone;
             const bool valid = inrow && c0 != kNumberedCls;
+            // the neighbour's class size and predecessor, read before x is
+            // numbered: f has lost x, and a dropped f makes the head g_after's
+            // predecessor
+            int csz = 0, cpv = 0;
+            if (valid) {
+                csz = c0 == f ? fsize : s.csize[c0];
+                cpv = (nx == kNone && c0 == g_after) ? HEAD : s.cprev[c0];
+                if (parent) parent[y] = x;
+            }
             // next pivot: the lowest moved vertex of the top class f; else f's
             // next member; else (f emptied) the lowest moved vertex of the class
             // after f, or its first member
             int src_lane = -1;     // lane holding the next pivot when it is a moved vertex
             bool via_nx = false;   // the next pivot is x's successor in f (f did not split)
+            bool via_ga = false;   // the next pivot is the first member of the untouched class after f
+            int d_nx = kNone, d_size = 0, d_ga = kNone;
             {
                 const unsigned inf = __ballot_sync(kFull, valid && c0 == f);
                 if (inf) {
@@ -422,22 +448,24 @@ __global__ void __launch_bounds__(kCsrThreads) lexbfs_csr_kernel(int *ws, int n,
                     via_nx = true;
                 } else if (g_after != kNone) {
                     const unsigned ing = __ballot_sync(kFull, valid && c0 == g_after);
-                    if (ing) src_lane = __ffs(ing) - 1;
-                    next_x = ing ? __shfl_sync(kFull, y, src_lane) : s.cfirst[g_after];
+                    if (ing) {
+                        src_lane = __ffs(ing) - 1;
+                        next_x = __shfl_sync(kFull, y, src_lane);
+                    } else {
+                        next_x = d_first;
+                        via_ga = true;
+                        d_size = s.csize[g_after];
+                        d_ga = s.cnext[g_after];
+                    }
                 }
                 if (next_x >= 0) {   // fetch its row now, overlapping the rest of the step
                     pbeg = row_ptr[next_x];
                     pend = row_ptr[next_x + 1];
+                    if (via_ga) d_nx = s.vnext[next_x];
                     pcol = (pend - pbeg <= 32 && pbeg + lane < pend) ? col[pbeg + lane] : -1;
                 }
             }
             number_x();
-            int csz = 0, cpv = 0;
-            if (valid) {
-                csz = s.csize[c0];
-                cpv = s.cprev[c0];
-                if (parent) parent[y] = x;
-            }
             const unsigned grp = __match_any_sync(kFull, valid ? c0 : kNumberedCls);
             const unsigned vmask = __ballot_sync(kFull, valid);
             const unsigned g = valid ? grp : 0u;
@@ -480,6 +508,16 @@ __global__ void __launch_bounds__(kCsrThreads) lexbfs_csr_kernel(int *ws, int n,
                 cf_nx = nnx;
                 cf_size = fsize;
                 carry = true;
+            } else if (via_ga) {
+                cf_f = g_after;
+                cf_nx = d_nx;
+                cf_size = d_size;
+                carry = true;
+                // the class after g_after once this step's new classes are in
+                // place: a split class there now has its new part in front
+                const unsigned hit = __ballot_sync(kFull, split && c0 == d_ga);
+                ga = hit ? __shfl_sync(kFull, cn, __ffs(hit) - 1) : d_ga;
+                ga_known = true;
             }
             __syncwarp();
             if (first && split) {
@@ -539,14 +577,14 @@ __global__ void __launch_bounds__(kCsrThreads) lexbfs_csr_kernel(int *ws, int n,
 
 size_t lexbfs_csr_workspace_bytes(int64_t n, int64_t max_deg) { return csr_state_stride_bytes(n, max_deg) + 256; }
 
-int lexbfs_csr_launch(int n, int64_t max_deg, const int64_t *row_ptr, const int32_t *col, int32_t *order,
+int lexbfs_csr_launch(int n, int64_t max_deg, const int64_t *row_ptr, const int32_t *col, int64_t nnz, int32_t *order,
                       int32_t *pos, int32_t *parent, void *ws, int num_sms, cudaStream_t stream) {
     if (n <= 0) return CG_OK;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms * 4));
     csr_init_kernel<<<blocks, 256, 0, stream>>>(static_cast<int *>(ws), n, max_deg, parent);
     CG_LAUNCH_CHECK("csr_init_kernel");
-    lexbfs_csr_kernel<<<1, kCsrThreads, 0, stream>>>(static_cast<int *>(ws), n, max_deg, row_ptr, col, order, pos,
-                                                     parent);
+    lexbfs_csr_kernel<<<1, kCsrThreads, 0, stream>>>(static_cast<int *>(ws), n, max_deg, row_ptr, col, nnz, order,
+                                                     pos, parent);
     CG_LAUNCH_CHECK("lexbfs_csr_kernel");
     return CG_OK;
 }

@@ -227,7 +227,7 @@ csr_part:
         unsigned long long *key = reinterpret_cast<unsigned long long *>(base + take(8));
         void *state = base + take(lexbfs_csr_workspace_bytes(n, n));
         if (dry) continue;
-        if (n > 0 && (rc = lexbfs_csr_launch(n, n, r.g.csr.row_ptr, r.g.csr.col, order, pos, parent, state,
+        if (n > 0 && (rc = lexbfs_csr_launch(n, n, r.g.csr.row_ptr, r.g.csr.col, r.g.csr.nnz, order, pos, parent, state,
                                              ctx->num_sms, s.stream)))
             return rc;
         if ((rc = peo_csr_launch(n, r.g.csr.row_ptr, r.g.csr.col, order, pos, parent, true, key, ctx->num_sms,

@@ -53,3 +53,4 @@ def test_version_and_null_checks(lib):
     assert B.cg_chordal_test_dense(None, None, None, None, None) == B.CG_EINVAL
     assert b"context" in B.cg_last_error_string()
     assert B.cg_context_create(None, None) == B.CG_EINVAL
+    assert B.cg_step_floor(None, 1024, 16, 1 << 20, 16, None, None) == B.CG_EINVAL

@@ -232,3 +232,18 @@ def test_variant_size_limits(ctx, n):
     h.rows[0, (n - 1) >> 5] |= np.uint32(1 << ((n - 1) & 31))
     h.rows[n - 1, 0] |= np.uint32(1)
     assert_parity(ctx, h)
+
+
+@pytest.mark.gpu
+def test_step_floor_probe():
+    """The latency-floor probe returns positive, ordered times and rejects bad
+    arguments with CG_EINVAL."""
+    with B.Context(0) as ctx:
+        f = B.step_floor(ctx, threads=256, iters=2048, chain_bytes=1 << 20, loads=4096)
+        assert f["chain_bytes"] == 1 << 20
+        assert 0 < f["barrier_pair_ns"] < 10_000
+        assert 0 < f["load_ns"] < 100_000
+        with pytest.raises(B.ChordalError):
+            B.step_floor(ctx, threads=100)
+        with pytest.raises(B.ChordalError):
+            B.step_floor(ctx, chain_bytes=64)
