@@ -47,24 +47,37 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _bind(path: str) -> ctypes.CDLL:
+    """Load a build of oracle.c and declare its entry points."""
+    lib = ctypes.CDLL(path)
+    P, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.or_lexbfs_csr.argtypes = [i32, P, P, P]
+    lib.or_lexbfs_dense.argtypes = [i32, i32, P, P]
+    lib.or_peo_check_csr.argtypes = [i32, P, P, P, P, P]
+    lib.or_peo_check_dense.argtypes = [i32, i32, P, P, P, P]
+    lib.or_chordal_test_csr.argtypes = [i32, P, P, P, P, P]
+    lib.or_chordal_test_dense.argtypes = [i32, i32, P, P, P, P]
+    lib.or_lexbfs_rank_csr.argtypes = [i32, P, P, P, i32, P]
+    lib.or_lexbfs_rank_dense.argtypes = [i32, i32, P, P, i32, P]
+    lib.or_mcs_csr.argtypes = [i32, P, P, P]
+    lib.or_mcs_dense.argtypes = [i32, i32, P, P]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P, i32 = ctypes.c_void_p, ctypes.c_int32
-            lib.or_lexbfs_csr.argtypes = [i32, P, P, P]
-            lib.or_lexbfs_dense.argtypes = [i32, i32, P, P]
-            lib.or_peo_check_csr.argtypes = [i32, P, P, P, P, P]
-            lib.or_peo_check_dense.argtypes = [i32, i32, P, P, P, P]
-            lib.or_chordal_test_csr.argtypes = [i32, P, P, P, P, P]
-            lib.or_chordal_test_dense.argtypes = [i32, i32, P, P, P, P]
-            lib.or_lexbfs_rank_csr.argtypes = [i32, P, P, P, i32, P]
-            lib.or_lexbfs_rank_dense.argtypes = [i32, i32, P, P, i32, P]
-            lib.or_mcs_csr.argtypes = [i32, P, P, P]
-            lib.or_mcs_dense.argtypes = [i32, i32, P, P]
-            _lib = lib
+            _lib = _bind(build())
     return _lib
+
+
+def use_library(path: str) -> None:
+    """Point the oracle at another build of oracle.c (the planted-mistake tests
+    load deliberately broken copies this way, in a child process)."""
+    global _lib
+    with _lock:
+        _lib = _bind(path)
 
 
 def _p(a: np.ndarray):
