@@ -364,9 +364,10 @@ __global__ void __launch_bounds__(kCsrThreads) lexbfs_csr_kernel(int *ws, int n,
     // saves two dependent loads at the start of most steps
     bool carry = false;
     int cf_f = 0, cf_nx = 0, cf_size = 0;
-    // the class after the pivot's class, carried when that class holds only
-    // the pivot (the common case on sparse graphs): the step that chose the
-    // pivot read it and corrected it for its own splits
+    // the class after the pivot's class, carried from a step whose next pivot
+    // was the first member of the untouched class after its own (the common
+    // case on sparse graphs): that step read it and corrected it for its own
+    // splits; it is needed when the pivot's class holds only the pivot
     bool ga_known = false;
     int ga = kNone;
     for (int i = 0; i < n; ++i) {
