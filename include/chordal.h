@@ -181,9 +181,10 @@ int cg_chordal_test_mcs_dense(cg_context *ctx, const cg_dense *g, cg_result *res
 
 /*
  * LexBFS order of a CSR graph (Section 4.2 in its O(N + M) form: each class a
- * list sorted by id, only the pivot's neighbours move).  One warp walks the n
- * steps with the partition state in the context workspace (about 84 B per
- * vertex, L2-resident for n ~ 1M).
+ * list sorted by id, only the pivot's neighbours move).  One CTA walks the n
+ * steps (warp 0; all its warps for rows longer than 32 neighbours) with the
+ * partition state in the context workspace: 60 n bytes plus 8 bytes per
+ * sort key slot (the next power of two >= n), 68-76 B per vertex.
  *   g      device CSR graph (sorted, symmetric, no loops; checked only when
  *          cfg.validate, which then synchronises the stream)
  *   order  device int32[n] (written);  pos  device int32[n] (written) or NULL
