@@ -35,7 +35,10 @@ Timing: inputs resident in HBM; before every timed step a 256 MiB buffer is
 written to flush L2; each step is bracketed by CUDA events on the launching
 stream.  `e2e` repeats the metric through the public API with pinned host
 inputs copied in and results copied out inside the timed region.
-`cpu_baseline` times the CPU oracle on a bounded sample.  With N > 1
+`cpu_baseline` times the CPU oracle on a bounded sample.  For the
+single-pair workloads `phases.floor` adds the step's latency floors measured
+after the timed region (`cg_step_floor`: a CTA barrier pair, a dependent load
+over a 32 MiB and a 1 GiB chain).  With N > 1
 (torchrun) every rank runs its own replica (one graph's test does not shard);
 value = tests on all ranks / max time over ranks.
 """
