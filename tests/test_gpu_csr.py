@@ -71,6 +71,16 @@ def test_random(ctx, n, p):
         assert_parity(ctx, gg.dense_to_csr(gg.random_dense(n, p, n + s)))
 
 
+@pytest.mark.parametrize("n,p", [(20, 0.15), (30, 0.1), (40, 0.08), (60, 0.05), (80, 0.04), (120, 0.03)])
+def test_sparse_small_random(ctx, n, p):
+    """Average degree 2-3: most steps find the top class holding only the
+    pivot and take the next pivot from the untouched class after it, and in
+    many of these graphs a step also splits the class after that one (the
+    case where the carried next class must be replaced by the new part)."""
+    for s in range(30):
+        assert_parity(ctx, gg.dense_to_csr(gg.random_dense(n, p, s)), f"seed {s}")
+
+
 def test_long_rows_multi_chunk(ctx):
     """Rows far longer than 32 neighbours exercise the per-class carries."""
     for n, p in ((200, 0.6), (500, 0.3)):
