@@ -924,8 +924,11 @@ def step_floor(ctx, stream, ns_per_step: float) -> dict:
     chain (L2-resident, like the 32 MiB dense graph) and over a 1 GiB chain
     (mostly DRAM)."""
     from paper_1508_06329_gb300 import binding as B
-    l2 = B.step_floor(ctx, threads=1024, iters=16384, chain_bytes=32 << 20, loads=100000, stream=stream)
-    dram = B.step_floor(ctx, threads=1024, iters=1024, chain_bytes=1 << 30, loads=20000, stream=stream)
+    try:
+        l2 = B.step_floor(ctx, threads=1024, iters=16384, chain_bytes=32 << 20, loads=100000, stream=stream)
+        dram = B.step_floor(ctx, threads=1024, iters=1024, chain_bytes=1 << 30, loads=20000, stream=stream)
+    except B.ChordalError as e:   # an auxiliary figure: the benchmark line is printed without it
+        return {"error": str(e)}
     floor = l2["barrier_pair_ns"] + l2["load_ns"]
     return {"barrier_pair_ns": l2["barrier_pair_ns"], "l2_load_ns": l2["load_ns"], "dram_load_ns": dram["load_ns"],
             "barrier_pair_plus_l2_load_ns": floor, "step_over_that": ns_per_step / floor,
