@@ -397,8 +397,9 @@ int cg_queue_create(cg_context *ctx, const cg_queue_config *cfg, cg_queue **out)
     q->pool_bytes = align_up((size_t)q->cfg.mem_budget_bytes, kAlign);
     if (cudaMalloc(&q->pool, q->pool_bytes) != cudaSuccess) {
         cudaGetLastError();
+        const size_t want = q->pool_bytes;
         delete q;
-        return set_error(CG_ENOMEM, "queue pool of %zu bytes could not be allocated", q->pool_bytes);
+        return set_error(CG_ENOMEM, "queue pool of %zu bytes could not be allocated", want);
     }
     q->alloc.reset(q->pool_bytes);
     q->slots.resize(q->cfg.max_inflight);
