@@ -215,6 +215,8 @@ int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const in
             B.ctas = std::min(cnt, ctx->num_sms * fused_ctas_per_sm(B.fplan));
         } else {
             if ((rc = lexbfs_dense_plan(B.nmax, ctx->cfg.threads_override, &B.lplan))) return rc;
+            B.bulk = true;
+            for (int q = B.begin; q < B.end; ++q) B.bulk = B.bulk && peo_group_bulk_ok(L->descs[q]);
             const int by_smem =
                 B.lplan.smem_bytes ? (int)std::max<size_t>(1, (228 * 1024) / (B.lplan.smem_bytes + 1024)) : 32;
             const int by_threads = std::max(1, 2048 / B.lplan.threads);
@@ -232,7 +234,10 @@ BatchBuffers batch_buffers(const BatchLayout &L, bool need_order) {
     bb.o_order = cv.take<int32_t>(need_order ? L.total : 0);
     bb.o_pos = cv.take<int32_t>(L.total);
     bb.o_parent = cv.take<int32_t>(L.total);
-    bb.o_keys = cv.take<unsigned long long>(L.count + 1);   // + the check's block counter (bucket 9 is last)
+    bb.o_cpar = cv.take<int32_t>(L.bk[9].end > L.bk[9].begin ? L.total : 0);
+    bb.o_ppos = cv.take<int32_t>(L.total);
+    // + the check's CTA counter and error word (bucket 9 is last)
+    bb.o_keys = cv.take<unsigned long long>(L.count + 2);
     bb.o_counter = cv.take<int>(kBuckets * 64);
     const auto &B9 = L.bk[9];
     bb.o_gstate = cv.take<unsigned char>(B9.end > B9.begin ? B9.lplan.gstate_bytes * B9.ctas : 0);
@@ -250,7 +255,6 @@ int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
     cg_context *tctx = account ? ctx : nullptr;   // timers and launch counts only for the caller's thread
     auto P = [&](size_t off) { return base + off; };
     const DenseDesc *ddesc = reinterpret_cast<const DenseDesc *>(P(bb.o_desc));
-    const int64_t *dvoff = reinterpret_cast<const int64_t *>(P(bb.o_voff));
     int32_t *order = orders ? orders : reinterpret_cast<int32_t *>(P(bb.o_order));
     int32_t *pos = reinterpret_cast<int32_t *>(P(bb.o_pos));
     int32_t *parent = reinterpret_cast<int32_t *>(P(bb.o_parent));
@@ -271,20 +275,22 @@ int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
                 return rc;
             if (account) ctx->launches += 1;
         } else {
+            CheckFeed feed{reinterpret_cast<int32_t *>(P(bb.o_cpar)),
+                           reinterpret_cast<int32_t *>(P(bb.o_ppos)), reinterpret_cast<uint32_t *>(P(bb.o_emask)),
+                           keys + B.begin};
             {
                 PhaseTimer pt(tctx, &ctx->ev_lex, s);
                 if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, parent,
                                               B.lplan.gstate_bytes ? P(bb.o_gstate) : nullptr, counters + 64 * b, s,
-                                              1)))
+                                              kParentExact, &feed)))
                     return rc;
             }
             PhaseTimer pt(tctx, &ctx->ev_check, s);
-            // the check over this bucket's vertices (a slice of the offset table)
-            if ((rc = peo_dense_launch(ddesc + B.begin, DenseDesc{}, cnt, dvoff + B.begin, B.vend - B.vbegin, order,
-                                       pos, parent, false, keys + B.begin, ctx->num_sms, s,
-                                       reinterpret_cast<uint32_t *>(P(bb.o_emask)), B.nmax, true, res)))
+            // the position-ordered check of this bucket's graphs
+            if ((rc = peo_group_launch(ddesc + B.begin, DenseDesc{}, cnt, B.nmax, B.bulk, order, feed.ppos, feed.emask,
+                                       keys + B.begin, res, s)))
                 return rc;
-            if (account) ctx->launches += 3;
+            if (account) ctx->launches += 2;
         }
         CG_CUDA_TRY(cudaEventRecord(ss.join[b], s));
         CG_CUDA_TRY(cudaStreamWaitEvent(stream, ss.join[b], 0));
@@ -320,13 +326,15 @@ int upload_layout(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
 
 // Workspace layout of run_single_dense (also the start of the host entry's).
 struct SingleDenseCarve {
-    size_t o_order, o_pos, o_parent, o_key, o_counter, o_gstate, o_emask;
+    size_t o_order, o_pos, o_parent, o_cpar, o_ppos, o_key, o_counter, o_gstate, o_emask;
     Carve cv;
     SingleDenseCarve(int n, const LexPlan &plan) {
         o_order = cv.take<int32_t>(n);
         o_pos = cv.take<int32_t>(n);
         o_parent = cv.take<int32_t>(n);
-        o_key = cv.take<unsigned long long>(2);
+        o_cpar = cv.take<int32_t>(n);
+        o_ppos = cv.take<int32_t>(n);
+        o_key = cv.take<unsigned long long>(3);   // key, the check's CTA counter, error word
         o_counter = cv.take<int>(1);
         o_gstate = cv.take<unsigned char>(plan.gstate_bytes);
         o_emask = cv.take<uint32_t>(earlier_mask_words(n));
@@ -335,35 +343,40 @@ struct SingleDenseCarve {
 
 // LexBFS and (optionally) the check for one graph given by value.
 int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int32_t *pos_out, cg_result *res,
-                     int32_t *parent_out, cudaStream_t stream) {
+                     cudaStream_t stream) {
     const int n = g->n;
     LexPlan plan;
     int rc = lexbfs_dense_plan(n, ctx->cfg.threads_override, &plan);
     if (rc) return rc;
     const SingleDenseCarve sc(n, plan);
-    const size_t o_order = sc.o_order, o_pos = sc.o_pos, o_parent = sc.o_parent, o_key = sc.o_key;
-    const size_t o_counter = sc.o_counter, o_gstate = sc.o_gstate, o_emask = sc.o_emask;
     if ((rc = ensure_ws(ctx, sc.cv.off))) return rc;
-    int32_t *order = order_out ? order_out : at<int32_t>(ctx, o_order);
-    int32_t *pos = pos_out ? pos_out : at<int32_t>(ctx, o_pos);
-    int32_t *parent = parent_out ? parent_out : at<int32_t>(ctx, o_parent);
+    int32_t *order = order_out ? order_out : at<int32_t>(ctx, sc.o_order);
+    int32_t *pos = pos_out ? pos_out : at<int32_t>(ctx, sc.o_pos);
+    int32_t *parent = at<int32_t>(ctx, sc.o_parent);
+    unsigned long long *key = at<unsigned long long>(ctx, sc.o_key);
     const DenseDesc d = desc_of(g, 0, 0);
-    if (n > 0) {
+    if (n == 0) {
+        if (!res) return CG_OK;
+        PhaseTimer pt(ctx, &ctx->ev_check, stream);
+        ctx->launches += 1;
+        return peo_dense_launch(nullptr, d, 1, nullptr, 0, order, pos, parent, true, key, ctx->num_sms, stream,
+                                nullptr, 0, false, res);
+    }
+    // with a result wanted, the search also leaves what the check needs: exact
+    // parents (by vertex and by position), the earlier-than masks and the keys
+    CheckFeed feed{at<int32_t>(ctx, sc.o_cpar), at<int32_t>(ctx, sc.o_ppos), at<uint32_t>(ctx, sc.o_emask), key};
+    {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
-        // the search records the parents of pivots that neighbour the previous
-        // pivot (one store per step); the check finds the rest
-        rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, res ? parent : nullptr,
-                                 plan.gstate_bytes ? at<void>(ctx, o_gstate) : nullptr, at<int>(ctx, o_counter), stream,
-                                 1);
+        rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, nullptr,
+                                 plan.gstate_bytes ? at<void>(ctx, sc.o_gstate) : nullptr, at<int>(ctx, sc.o_counter),
+                                 stream, res ? kParentExact : kParentMoves, res ? &feed : nullptr);
         if (rc) return rc;
         ctx->launches += 1;
     }
     if (!res) return CG_OK;
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
-    unsigned long long *key = at<unsigned long long>(ctx, o_key);
-    ctx->launches += n > 0 ? 2 : 1;
-    return peo_dense_launch(nullptr, d, 1, nullptr, n, order, pos, parent, false, key, ctx->num_sms, stream,
-                            at<uint32_t>(ctx, o_emask), n, true, res);
+    ctx->launches += 1;
+    return peo_group_launch(nullptr, d, 1, n, peo_group_bulk_ok(d), order, feed.ppos, feed.emask, key, res, stream);
 }
 
 // Optional layout check of a CSR graph (synchronises the stream).
@@ -501,7 +514,7 @@ int cg_lexbfs_order_dense(cg_context *ctx, const cg_dense *g, int32_t *order, in
     int rc;
     if ((rc = check_ctx(ctx)) || (rc = check_dense(g))) return rc;
     if (g->n > 0 && !order) return set_error(CG_EINVAL, "null order pointer");
-    return run_single_dense(ctx, g, order, pos, nullptr, nullptr, stream);
+    return run_single_dense(ctx, g, order, pos, nullptr, stream);
 }
 
 int cg_lexbfs_sweep_dense(cg_context *ctx, const cg_dense *g, int32_t kind, const int32_t *tiebreak, int32_t start,
@@ -514,7 +527,7 @@ int cg_lexbfs_sweep_dense(cg_context *ctx, const cg_dense *g, int32_t kind, cons
         return set_error(CG_EINVAL, "unknown tie-break kind %d", kind);
     if (kind != CG_TIE_ID && n > 0 && !tiebreak) return set_error(CG_EINVAL, "null tie-break array");
     if (start < -1 || (start >= 0 && start >= n)) return set_error(CG_EINVAL, "start %d outside [-1, n)", start);
-    if (kind == CG_TIE_ID && start < 0) return run_single_dense(ctx, g, order, pos, nullptr, nullptr, stream);
+    if (kind == CG_TIE_ID && start < 0) return run_single_dense(ctx, g, order, pos, nullptr, stream);
     if (n == 0) return CG_OK;
     LexPlan plan;
     if ((rc = lexbfs_dense_plan(n, ctx->cfg.threads_override, &plan))) return rc;
@@ -591,7 +604,7 @@ int cg_chordal_test_dense(cg_context *ctx, const cg_dense *g, cg_result *res, in
     int rc;
     if ((rc = check_ctx(ctx)) || (rc = check_dense(g))) return rc;
     if (!res) return set_error(CG_EINVAL, "null result pointer");
-    return run_single_dense(ctx, g, order, nullptr, res, nullptr, stream);
+    return run_single_dense(ctx, g, order, nullptr, res, stream);
 }
 
 int cg_peo_check_dense(cg_context *ctx, const cg_dense *g, const int32_t *order, int32_t *parent, cg_result *res,
@@ -649,7 +662,7 @@ int cg_chordal_test_dense_host(cg_context *ctx, int32_t n, int32_t words_per_row
     int32_t *order = at<int32_t>(ctx, o_order);
     if (bytes_rows) CG_CUDA_TRY(cudaMemcpyAsync(rows, host_rows, bytes_rows, cudaMemcpyHostToDevice, stream));
     cg_dense g{n, words_per_row, rows};
-    if ((rc = run_single_dense(ctx, &g, order, nullptr, res, nullptr, stream))) return rc;
+    if ((rc = run_single_dense(ctx, &g, order, nullptr, res, stream))) return rc;
     CG_CUDA_TRY(cudaMemcpyAsync(host_res, res, sizeof(cg_result), cudaMemcpyDeviceToHost, stream));
     if (host_order && n > 0)
         CG_CUDA_TRY(cudaMemcpyAsync(host_order, order, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, stream));

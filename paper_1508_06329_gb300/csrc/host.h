@@ -87,6 +87,7 @@ struct BatchLayout {
         FusedPlan fplan{};
         LexPlan lplan{};
         int ctas = 0;
+        bool bulk = false;              // bucket 9: every graph's rows suit bulk copies
         int64_t vbegin = 0, vend = 0;   // packed vertex range
     };
     int count = 0;
@@ -99,7 +100,7 @@ struct BatchLayout {
 
 // Device buffers a batch needs (offsets into one allocation).
 struct BatchBuffers {
-    size_t o_desc, o_voff, o_order, o_pos, o_parent, o_keys, o_counter, o_gstate, o_emask, bytes;
+    size_t o_desc, o_voff, o_order, o_pos, o_parent, o_cpar, o_ppos, o_keys, o_counter, o_gstate, o_emask, bytes;
 };
 
 int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const int64_t *order_offsets,

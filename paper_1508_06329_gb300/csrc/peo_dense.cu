@@ -31,7 +31,8 @@ constexpr int kPeoThreads = 256;
 constexpr int kRC = 8;    // row words per lane held in registers (256 words = 8,192 vertices per chunk)
 
 // "Earlier-than" masks: for each group b of 32 positions, E_b has bit u set
-// iff pos(u) < 32 b.  ceil(n/32)^2 words per graph at emask + ebase, row b = E_b.
+// iff pos(u) < 32 b.  ceil(n/32) rows of mask_stride(n) words per graph at
+// emask + ebase, row b = E_b.
 constexpr int kMaskRows = 32;         // rows b per mask tile
 constexpr int kScan = 32;             // positions a prep thread scans for p(v)
 
@@ -121,7 +122,8 @@ __global__ void __launch_bounds__(kPeoThreads, 4) peo_dense_kernel(const DenseDe
         const int pv = __ldg(pos_g + v);
         if (pv < 0 || pv >= d.n) continue;   // not in the order (only for an invalid caller order)
         const uint32_t *rv = d.rows + (size_t)v * d.words;
-        const uint32_t *E = emask ? emask + d.ebase + (size_t)(pv >> 5) * wn : nullptr;
+        const int es = mask_stride(d.n);
+        const uint32_t *E = emask ? emask + d.ebase + (size_t)(pv >> 5) * es : nullptr;
 
         uint32_t ae[kRC];   // row_v & E_b of one chunk
         auto load_ae = [&](int w0) {
@@ -160,12 +162,12 @@ __global__ void __launch_bounds__(kPeoThreads, 4) peo_dense_kernel(const DenseDe
                     if (p < 0 && c >= 0) {
                         // groups 0..c remain: F(g) = |row_v ∩ E_g| is nondecreasing in g; the
                         // parent's group is the last g <= c with F(g) < F(c + 1)
-                        const int total = count_in(rv, emask + d.ebase + (size_t)(c + 1) * wn, wn, lane);
+                        const int total = count_in(rv, emask + d.ebase + (size_t)(c + 1) * es, wn, lane);
                         if (total > 0) {
                             int lo = 0, hi = c + 1;   // F(lo) < total = F(hi)
                             while (hi - lo > 1) {
                                 const int mid = (lo + hi) >> 1;
-                                if (count_in(rv, emask + d.ebase + (size_t)mid * wn, wn, lane) == total) hi = mid;
+                                if (count_in(rv, emask + d.ebase + (size_t)mid * es, wn, lane) == total) hi = mid;
                                 else lo = mid;
                             }
                             const int u = __ldg(ord_g + lo * 32 + lane);
@@ -275,6 +277,7 @@ __global__ void peo_prep_kernel(const DenseDesc *__restrict__ descs, DenseDesc s
         const int wcols = (wn + 31) >> 5, brows = (wn + kMaskRows - 1) / kMaskRows;
         const int64_t tiles = (int64_t)wcols * brows;
         uint32_t *E = emask + d.ebase;
+        const int es = mask_stride(n);
         for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < tiles;
              tile += ((int64_t)mask_blocks * blockDim.x) >> 5) {
             const int wc = (int)(tile % wcols), br = (int)(tile / wcols);
@@ -302,7 +305,7 @@ __global__ void peo_prep_kernel(const DenseDesc *__restrict__ descs, DenseDesc s
                 uint32_t word = 0u;
 #pragma unroll
                 for (int k = 0; k < 32; ++k) word |= (grp[k] < (uint32_t)b ? 1u : 0u) << k;
-                if (w < wn) E[(size_t)b * wn + w] = word;
+                if (w < wn) E[(size_t)b * es + w] = word;
             }
         }
         return;
@@ -365,6 +368,230 @@ __global__ void invert_order_kernel(const DenseDesc *__restrict__ descs, DenseDe
     }
 }
 
+// ---- the check of a search's own order, positions in order (fed by the search)
+//
+// One CTA takes kSub consecutive positions s0 .. s0 + kSub - 1 of one graph
+// (blockIdx.y).  The search left p(v) by position (exact), the order, and
+// E_b for the group b = s0 / 32 (the vertices numbered before position 32 b),
+// so nothing is searched here: the CTA stages, per round of kChunkWords row
+// words, row v of each of its positions, row p(v) of the parents that are not
+// among its own vertices (for a LexBFS order p(v) is mostly the previous
+// pivot, i.e. the row staged just before) and the mask row E_b in shared
+// memory — one bulk copy each, all completing on one mbarrier — then each
+// warp tests its vertices:
+//   bad(v) = (row_v & ~row_p & E_b, without p) ∪ {u at positions 32 b ..
+//            pos(v) - 1 : u ∈ N(v), u != p, u ∉ N(p)}
+// and the first violation in order is kept by a 64-bit atomicMin of
+// (pos(v) << 32 | min bad(v)).  The last CTA to finish writes the results.
+constexpr unsigned kNoBad = 0xFFFFFFFFu;    // no bad vertex found
+constexpr int kGrpThreads = 256;
+constexpr int kSub = 16;                       // positions per CTA (2 per warp)
+constexpr int kExt = 8;                        // staged parent rows outside the CTA's own rows
+constexpr int kChunkWords = 512;               // row words staged per row and round (2 KiB)
+constexpr int kMaskSlot = kSub + kExt;         // slot of E_b
+constexpr int kSlots = kSub + kExt + 1;
+constexpr size_t kGrpSmemBytes = (size_t)kSlots * kChunkWords * sizeof(uint32_t);
+
+// (chordal, v, p, u) from a key, with the parent by position; chordal = -1
+// when the check could not complete (err != 0: 1 a bounded wait gave up, 2 an
+// order or parent value outside 0..n-1).
+__device__ __forceinline__ void write_result_ppos(const DenseDesc &d, unsigned long long k, unsigned long long err,
+                                                  const int32_t *order, const int32_t *ppos, cg_result *out) {
+    cg_result r;
+    if (err) {
+        r.chordal = -1;
+        r.v = r.p = r.u = -1;
+    } else if (k == ~0ull) {
+        r.chordal = 1;
+        r.v = r.p = r.u = -1;
+    } else {
+        const int i = (int)(k >> 32);
+        r.chordal = 0;
+        r.v = order[d.obase + i];
+        r.p = ppos[d.vbase + i];
+        r.u = (int)(k & 0xFFFFFFFFu);
+    }
+    *out = r;
+}
+
+template <bool BULK>
+__global__ void __launch_bounds__(kGrpThreads) peo_group_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
+                                                                int count, const int32_t *__restrict__ order,
+                                                                const int32_t *__restrict__ ppos,
+                                                                const uint32_t *__restrict__ emask,
+                                                                unsigned long long *__restrict__ keys,
+                                                                cg_result *__restrict__ res) {
+    extern __shared__ __align__(128) uint32_t sbuf[];   // kSlots rows of kChunkWords words
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int s_v[32];         // vertices at the group's 32 positions (-1 past n)
+    __shared__ int s_p[kSub];       // p(v) of the CTA's positions (-1: none)
+    __shared__ int s_src[kSub];     // slot holding row p(v): j' < kSub own, kSub + e staged, -1 global
+    __shared__ int s_ext[kExt];     // vertex of each staged parent slot
+    __shared__ int s_next;
+    __shared__ bool s_last;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int gi = blockIdx.y;
+    const DenseDesc d = descs ? descs[gi] : single;
+    const int n = d.n;
+    const int s0 = blockIdx.x * kSub;
+    if (s0 < n) {
+        const int wn = (n + 31) >> 5;
+        const uint32_t lastmask = (n & 31) ? ((1u << (n & 31)) - 1u) : 0xFFFFFFFFu;
+        const int gstart = s0 & ~31;
+        const int nsub = min(kSub, n - s0);
+        // order and parents come from the search; a value outside 0..n-1 (only
+        // possible if those buffers were overwritten) is reported, never used
+        if (t < 32) {
+            int v = gstart + t < n ? __ldg(order + d.obase + gstart + t) : -1;
+            if (gstart + t < n && (unsigned)v >= (unsigned)n) {
+                atomicOr(keys + count + 1, 2ull);
+                v = 0;
+            }
+            s_v[t] = v;
+        } else if (t < 32 + kSub) {
+            const int j = t - 32;
+            int p = j < nsub ? __ldg(ppos + d.vbase + s0 + j) : -1;
+            if (p >= n || p < -1) {
+                atomicOr(keys + count + 1, 2ull);
+                p = -1;
+            }
+            s_p[j] = p;
+        } else if (t == 32 + kSub) {
+            s_next = 0;
+            if (BULK) {
+                mbar_init(&bar, 1);
+                fence_proxy_async_smem();
+            }
+        }
+        __syncthreads();
+        if (t < kSub) {   // where row p(v) comes from: p precedes v, so an own row has a lower slot
+            const int p = s_p[t];
+            int src = -1;
+            if (p >= 0) {
+                for (int k = 0; k < t; ++k)
+                    if (s_v[s0 - gstart + k] == p) src = k;
+                if (src < 0) {
+                    const int e = atomicAdd(&s_next, 1);
+                    if (e < kExt) {
+                        src = kSub + e;
+                        s_ext[e] = p;
+                    }
+                }
+            }
+            s_src[t] = src;
+        }
+        __syncthreads();
+        const int next = min(s_next, kExt);
+        const uint32_t *Eg = emask + d.ebase + (size_t)(s0 >> 5) * mask_stride(n);
+        unsigned umin[2] = {kNoBad, kNoBad};   // vertices j = warp and warp + 8
+        bool failed = false;
+        int round = 0;
+        for (int c0 = 0; c0 < wn; c0 += kChunkWords, ++round) {
+            const int cw = min(kChunkWords, wn - c0);
+            if (BULK) {
+                if (t == 0) {
+                    const uint32_t bytes = (uint32_t)((cw + 3) & ~3) * 4u;   // within the padded row (words % 4 == 0)
+                    mbar_arrive_expect_tx(&bar, bytes * (uint32_t)(nsub + next + 1));
+                    for (int j = 0; j < nsub; ++j)
+                        bulk_copy_g2s(sbuf + j * kChunkWords, d.rows + (size_t)s_v[s0 - gstart + j] * d.words + c0,
+                                      bytes, &bar);
+                    for (int e = 0; e < next; ++e)
+                        bulk_copy_g2s(sbuf + (kSub + e) * kChunkWords, d.rows + (size_t)s_ext[e] * d.words + c0, bytes,
+                                      &bar);
+                    bulk_copy_g2s(sbuf + kMaskSlot * kChunkWords, Eg + c0, bytes, &bar);
+                }
+                if (!mbar_wait_parity_bounded(&bar, round & 1)) failed = true;
+            } else {
+                const int rows_used = nsub + next + 1;
+                for (int idx = t; idx < rows_used * cw; idx += kGrpThreads) {
+                    const int r = idx / cw, w = idx - r * cw;
+                    const uint32_t *src;
+                    int slot;
+                    if (r < nsub) {
+                        slot = r;
+                        src = d.rows + (size_t)s_v[s0 - gstart + r] * d.words;
+                    } else if (r < nsub + next) {
+                        slot = kSub + (r - nsub);
+                        src = d.rows + (size_t)s_ext[r - nsub] * d.words;
+                    } else {
+                        slot = kMaskSlot;
+                        src = Eg;
+                    }
+                    sbuf[slot * kChunkWords + w] = __ldg(src + c0 + w);
+                }
+                __syncthreads();
+            }
+            if (__syncthreads_or(failed)) {   // a bounded wait gave up: report, do not test
+                if (t == 0) atomicOr(keys + count + 1, 1ull);
+                break;
+            }
+            const uint32_t *E = sbuf + kMaskSlot * kChunkWords;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int j = warp + 8 * q;
+                if (j >= nsub || umin[q] != kNoBad) continue;   // a hit in an earlier round has a lower id
+                const int p = s_p[j];
+                if (p < 0) continue;   // no earlier neighbour: LN_v is empty
+                const uint32_t *rv = sbuf + j * kChunkWords;
+                const int src = s_src[j];
+                const uint32_t *rps = src >= 0 ? sbuf + src * kChunkWords : nullptr;
+                const uint32_t *rpg = d.rows + (size_t)p * d.words + c0;
+                // earlier groups: the lowest bit of row_v & ~row_p & E_b, p excluded
+                unsigned m = kNoBad;
+                for (int w0 = 0; w0 < cw; w0 += 32) {   // warp-uniform trip count
+                    const int w = w0 + lane;
+                    if (w < cw) {
+                        const int gw = c0 + w;
+                        uint32_t bits = rv[w] & ~(rps ? rps[w] : __ldg(rpg + w)) & E[w];
+                        if (gw == wn - 1) bits &= lastmask;
+                        if (gw == (p >> 5)) bits &= ~(1u << (p & 31));
+                        if (bits) m = (unsigned)((gw << 5) + __ffs(bits) - 1);
+                    }
+                    if (__any_sync(0xFFFFFFFFu, m != kNoBad)) break;   // later words hold higher ids
+                }
+                // the group's own earlier positions 32 b .. pos(v) - 1, one per lane
+                if (gstart + lane < s0 + j) {
+                    const int u = s_v[lane];
+                    const int uw = (u >> 5) - c0;
+                    if (uw >= 0 && uw < cw && u != p) {
+                        const uint32_t bit = 1u << (u & 31);
+                        const uint32_t pw = rps ? rps[uw] : __ldg(rpg + uw);
+                        if ((rv[uw] & bit) && !(pw & bit)) m = min(m, (unsigned)u);
+                    }
+                }
+                m = __reduce_min_sync(0xFFFFFFFFu, m);
+                umin[q] = m;
+            }
+            if (c0 + kChunkWords < wn) {   // the next round overwrites the staged rows
+                __syncthreads();
+                if (BULK) fence_proxy_async_smem();
+            }
+        }
+        if (lane == 0 && !failed) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int j = warp + 8 * q;
+                if (j < nsub && umin[q] != kNoBad)
+                    atomicMin(keys + gi, ((unsigned long long)(unsigned)(s0 + j) << 32) | umin[q]);
+            }
+        }
+    }
+    // the last CTA to finish turns the keys into results (keys[count] counts CTAs)
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        s_last = atomicAdd(keys + count, 1ull) == (unsigned long long)gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        const unsigned long long err = atomicAdd(keys + count + 1, 0ull);
+        for (int g = t; g < count; g += kGrpThreads)
+            write_result_ppos(descs ? descs[g] : single, atomicAdd(keys + g, 0ull), err, order, ppos,
+                              res + (descs ? descs[g].rindex : g));
+    }
+}
+
 }  // namespace
 
 int invert_order_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
@@ -388,7 +615,7 @@ int order_check_launch(int n, const int32_t *order, int *seen, int *flag, int nu
 
 int64_t earlier_mask_words(int n) {
     const int64_t wn = (n + 31) / 32;
-    return wn * wn;
+    return wn * mask_stride(n);
 }
 
 int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
@@ -428,6 +655,32 @@ int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const 
                                                                     parent, emask, keys, fres);
     CG_LAUNCH_CHECK("peo_dense_kernel");
     if (res && !fused) return finalize_launch(descs, single, count, keys, order, parent, res, stream);
+    return CG_OK;
+}
+
+bool peo_group_bulk_ok(const DenseDesc &d) {
+    return (reinterpret_cast<uintptr_t>(d.rows) & 15) == 0 && (d.words & 3) == 0 && (d.ebase & 3) == 0;
+}
+
+int peo_group_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, bool bulk, const int32_t *order,
+                     const int32_t *ppos, const uint32_t *emask, unsigned long long *keys, cg_result *res,
+                     cudaStream_t stream) {
+    if (count <= 0 || n_max <= 0) return set_error(CG_EINVAL, "position-ordered check needs count, n > 0");
+    if (count > 65535) return set_error(CG_EINVAL, "too many graphs for one check launch (%d)", count);
+    if ((reinterpret_cast<uintptr_t>(emask) & 15) != 0) return set_error(CG_EINVAL, "mask buffer not 16-byte aligned");
+    const dim3 grid((unsigned)ceil_div(n_max, kSub), (unsigned)count);
+    if (bulk) {
+        CG_CUDA_TRY(cudaFuncSetAttribute(peo_group_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kGrpSmemBytes));
+        peo_group_kernel<true><<<grid, kGrpThreads, kGrpSmemBytes, stream>>>(descs, single, count, order, ppos, emask,
+                                                                             keys, res);
+    } else {
+        CG_CUDA_TRY(cudaFuncSetAttribute(peo_group_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kGrpSmemBytes));
+        peo_group_kernel<false><<<grid, kGrpThreads, kGrpSmemBytes, stream>>>(descs, single, count, order, ppos,
+                                                                              emask, keys, res);
+    }
+    CG_LAUNCH_CHECK("peo_group_kernel");
     return CG_OK;
 }
 
