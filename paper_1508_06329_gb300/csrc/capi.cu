@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -185,18 +186,12 @@ int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const in
         packed += graphs[k].n;
     }
     for (int b = 0; b < kBuckets; ++b) L->bk[b] = BatchLayout::Bucket{};
-    int64_t eoff = 0;
     for (int j = 0; j < count; ++j) {
         const int k = idx[j];
         L->voff[j] = total;
         L->descs[j] = desc_of(&graphs[k], total, obase[k], k);
-        if (bucket[k] == 9) {   // graphs checked by the grid-wide kernel get earlier-than masks
-            L->descs[j].ebase = eoff;
-            eoff += earlier_mask_words(graphs[k].n);
-        }
         total += graphs[k].n;
     }
-    L->emask_words = eoff;
     L->voff[count] = total;
     L->total = total;
     int j = 0;
@@ -216,7 +211,7 @@ int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const in
         } else {
             if ((rc = lexbfs_dense_plan(B.nmax, ctx->cfg.threads_override, &B.lplan))) return rc;
             B.bulk = true;
-            for (int q = B.begin; q < B.end; ++q) B.bulk = B.bulk && peo_group_bulk_ok(L->descs[q]);
+            for (int q = B.begin; q < B.end; ++q) B.bulk = B.bulk && peo_rows_vec_ok(L->descs[q]);
             const int by_smem =
                 B.lplan.smem_bytes ? (int)std::max<size_t>(1, (228 * 1024) / (B.lplan.smem_bytes + 1024)) : 32;
             const int by_threads = std::max(1, 2048 / B.lplan.threads);
@@ -234,14 +229,12 @@ BatchBuffers batch_buffers(const BatchLayout &L, bool need_order) {
     bb.o_order = cv.take<int32_t>(need_order ? L.total : 0);
     bb.o_pos = cv.take<int32_t>(L.total);
     bb.o_parent = cv.take<int32_t>(L.total);
-    bb.o_cpar = cv.take<int32_t>(L.bk[9].end > L.bk[9].begin ? L.total : 0);
     bb.o_ppos = cv.take<int32_t>(L.total);
     // + the check's CTA counter and error word (bucket 9 is last)
     bb.o_keys = cv.take<unsigned long long>(L.count + 2);
     bb.o_counter = cv.take<int>(kBuckets * 64);
     const auto &B9 = L.bk[9];
     bb.o_gstate = cv.take<unsigned char>(B9.end > B9.begin ? B9.lplan.gstate_bytes * B9.ctas : 0);
-    bb.o_emask = cv.take<uint32_t>(L.emask_words);
     bb.bytes = cv.off;
     return bb;
 }
@@ -275,20 +268,18 @@ int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
                 return rc;
             if (account) ctx->launches += 1;
         } else {
-            CheckFeed feed{reinterpret_cast<int32_t *>(P(bb.o_cpar)),
-                           reinterpret_cast<int32_t *>(P(bb.o_ppos)), reinterpret_cast<uint32_t *>(P(bb.o_emask)),
-                           keys + B.begin};
+            int32_t *ppos = reinterpret_cast<int32_t *>(P(bb.o_ppos));
             {
                 PhaseTimer pt(tctx, &ctx->ev_lex, s);
-                if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, parent,
+                if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, ppos,
                                               B.lplan.gstate_bytes ? P(bb.o_gstate) : nullptr, counters + 64 * b, s,
-                                              kParentExact, &feed)))
+                                              kParentPivots, keys + B.begin)))
                     return rc;
             }
             PhaseTimer pt(tctx, &ctx->ev_check, s);
-            // the position-ordered check of this bucket's graphs
-            if ((rc = peo_group_launch(ddesc + B.begin, DenseDesc{}, cnt, B.nmax, B.bulk, order, feed.ppos, feed.emask,
-                                       keys + B.begin, res, s)))
+            // the position-ordered check of this bucket's graphs (masks, open parents, check)
+            if ((rc = peo_unit_launch(ddesc + B.begin, DenseDesc{}, cnt, B.nmax, B.bulk, order, pos, ppos,
+                                      keys + B.begin, res, s)))
                 return rc;
             if (account) ctx->launches += 2;
         }
@@ -326,18 +317,16 @@ int upload_layout(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
 
 // Workspace layout of run_single_dense (also the start of the host entry's).
 struct SingleDenseCarve {
-    size_t o_order, o_pos, o_parent, o_cpar, o_ppos, o_key, o_counter, o_gstate, o_emask;
+    size_t o_order, o_pos, o_parent, o_ppos, o_key, o_counter, o_gstate;
     Carve cv;
     SingleDenseCarve(int n, const LexPlan &plan) {
         o_order = cv.take<int32_t>(n);
         o_pos = cv.take<int32_t>(n);
         o_parent = cv.take<int32_t>(n);
-        o_cpar = cv.take<int32_t>(n);
         o_ppos = cv.take<int32_t>(n);
         o_key = cv.take<unsigned long long>(3);   // key, the check's CTA counter, error word
         o_counter = cv.take<int>(1);
         o_gstate = cv.take<unsigned char>(plan.gstate_bytes);
-        o_emask = cv.take<uint32_t>(earlier_mask_words(n));
     }
 };
 
@@ -362,21 +351,21 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
         return peo_dense_launch(nullptr, d, 1, nullptr, 0, order, pos, parent, true, key, ctx->num_sms, stream,
                                 nullptr, 0, false, res);
     }
-    // with a result wanted, the search also leaves what the check needs: exact
-    // parents (by vertex and by position), the earlier-than masks and the keys
-    CheckFeed feed{at<int32_t>(ctx, sc.o_cpar), at<int32_t>(ctx, sc.o_ppos), at<uint32_t>(ctx, sc.o_emask), key};
+    // with a result wanted, the search also records the parents of its pivots
+    // by position (one store per step) and initialises the check's keys
+    int32_t *ppos = at<int32_t>(ctx, sc.o_ppos);
     {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
-        rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, nullptr,
+        rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, res ? ppos : nullptr,
                                  plan.gstate_bytes ? at<void>(ctx, sc.o_gstate) : nullptr, at<int>(ctx, sc.o_counter),
-                                 stream, res ? kParentExact : kParentMoves, res ? &feed : nullptr);
+                                 stream, kParentPivots, res ? key : nullptr);
         if (rc) return rc;
         ctx->launches += 1;
     }
     if (!res) return CG_OK;
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
     ctx->launches += 1;
-    return peo_group_launch(nullptr, d, 1, n, peo_group_bulk_ok(d), order, feed.ppos, feed.emask, key, res, stream);
+    return peo_unit_launch(nullptr, d, 1, n, peo_rows_vec_ok(d), order, pos, ppos, key, res, stream);
 }
 
 // Optional layout check of a CSR graph (synchronises the stream).

@@ -33,58 +33,6 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// ---- bulk copies global -> shared memory (cp.async.bulk, completed on an mbarrier)
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t arrivals) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(arrivals) : "memory");
-}
-
-// Makes shared-memory writes of the generic proxy (and an mbarrier's
-// initialisation) visible to the bulk-copy engine.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// One arrival that also announces `bytes` of bulk-copy data for the phase.
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Copies `bytes` (a multiple of 16; both addresses 16-byte aligned) from
-// global memory into this CTA's shared memory; completion counts on `bar`.
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait_parity(unsigned long long *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Waits for the phase with the given parity to complete; gives up after
-// `limit` polls (each poll may suspend the thread for a short while) and
-// returns false then.
-__device__ __forceinline__ bool mbar_wait_parity_bounded(unsigned long long *bar, uint32_t parity,
-                                                         uint32_t limit = 1u << 22) {
-    for (uint32_t k = 0; k < limit; ++k)
-        if (mbar_try_wait_parity(bar, parity)) return true;
-    return false;
-}
-
 // Spreads bulk L2 prefetches of a contiguous range over the CTA's threads.
 template <int T>
 __device__ __forceinline__ void prefetch_range_l2(const void *base, size_t bytes) {
@@ -105,8 +53,8 @@ __device__ __forceinline__ void prefetch_range_l2(const void *base, size_t bytes
 constexpr int kParentUnresolved = -2;
 
 // How the dense LexBFS records parents (when given a parent array).
-constexpr int kParentMoves = 0;        // every moved vertex: parent[y] = pivot
-constexpr int kParentExact = 1;        // once per pivot, exact (per-class parents)
+constexpr int kParentMoves = 0;        // every moved vertex: parent[v] = pivot
+constexpr int kParentPivots = 1;       // once per step, by position: parent[i], or kParentUnresolved
 
 // Per-graph descriptor as the kernels see it (device memory).
 struct DenseDesc {
@@ -120,14 +68,6 @@ struct DenseDesc {
     int64_t ebase;          // word offset of this graph's earlier-than masks in the check's mask buffer
 };
 
-// Per-launch buffers of the search that feed the position-ordered check
-// (indexed like pos / parent by each graph's vbase; masks by its ebase).
-struct CheckFeed {
-    int32_t *cpar;                // per-class parents (scratch)
-    int32_t *ppos;                // parents by position
-    uint32_t *emask;              // earlier-than masks
-    unsigned long long *keys;     // [count] witness keys, [count] block counter, [count + 1] error word
-};
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

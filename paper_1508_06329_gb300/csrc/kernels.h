@@ -25,17 +25,15 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan);
 // Runs LexBFS for `count` graphs, one CTA each (grid = min(count, ctas)).
 // descs: device array, or nullptr to use `single` (count must be 1).
 // work_counter: device int, zeroed by the launcher (dynamic graph hand-out).
-// parent_mode 0 (kParentMoves): parent (packed by vbase, nullable) receives
-// p(v) for every vertex, a store per moved vertex.  1 (kParentExact): parent
-// is unused; the search stores p(order[i]) once per step into feed->ppos
-// (packed by vbase), from per-class parents kept in feed->cpar (packed by
-// vbase), and also writes the earlier-than masks (feed->emask, when
-// non-null, at each desc's ebase, rows of mask_stride(n) words) and the
-// check's initial keys (feed->keys, when non-null: keys[0..count) = "no
-// violation", keys[count] = keys[count + 1] = 0).
+// parent (packed by vbase) receives parents when non-null: parent_mode
+// kParentMoves records p(v) for every vertex (a store per moved vertex),
+// kParentPivots one value per step by position, parent[i] = p(order[i]), or
+// kParentUnresolved for the pivots chosen from the class after the top one.
+// keys (nullable) receives the check's initial keys: keys[0..count) = "no
+// violation", keys[count] = keys[count + 1] = 0.
 int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                         int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
-                        cudaStream_t stream, int parent_mode = 0, const CheckFeed *feed = nullptr);
+                        cudaStream_t stream, int parent_mode = 0, unsigned long long *keys = nullptr);
 
 // ---- dense perfect-elimination check (peo_dense.cu)
 // keys: device u64[count], set to ~0 by the launcher.
@@ -54,16 +52,17 @@ int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const 
                      int n_max = 0, bool prefilled = false, cg_result *res = nullptr);
 int64_t earlier_mask_words(int n);
 
-// The check of orders the dense LexBFS produced with kParentExact and a
-// CheckFeed (parents by position, earlier-than masks, keys initialised):
-// one CTA per 16 positions (grid ceil(n_max / 16) x count), rows staged in
-// shared memory (bulk copies when every graph passes peo_group_bulk_ok), the
-// last CTA writes res.  A result with chordal = -1 reports a bounded device
-// wait that gave up.
-bool peo_group_bulk_ok(const DenseDesc &d);
-int peo_group_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, bool bulk, const int32_t *order,
-                     const int32_t *ppos, const uint32_t *emask, unsigned long long *keys, cg_result *res,
-                     cudaStream_t stream);
+// The check of orders the dense LexBFS produced under kParentPivots (parents
+// by position in ppos, keys initialised by the search), in one launch: one
+// block per group of 32 positions (grid ceil(n_max / 32) x count) builds E_b
+// in shared memory from pos, resolves the group's open parents (stored back
+// into ppos) and checks its positions; its last block writes res.  vec when
+// every graph passes peo_rows_vec_ok (rows 16-byte aligned, words_per_row a
+// multiple of 4: 128-bit row loads).  A result with chordal = -1 reports a
+// check that could not complete (an order or parent value outside 0..n-1).
+bool peo_rows_vec_ok(const DenseDesc &d);
+int peo_unit_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, bool vec, const int32_t *order,
+                    const int32_t *pos, int32_t *ppos, unsigned long long *keys, cg_result *res, cudaStream_t stream);
 // sets *flag when order is not a permutation of 0..n-1 (seen: n ints of scratch)
 int order_check_launch(int n, const int32_t *order, int *seen, int *flag, int num_sms, cudaStream_t stream);
 

@@ -13,21 +13,18 @@ constexpr int kSmemMaxN = 16384;             // 16-bit ids, whole state in share
 constexpr int kSplitMaxN = 65520;            // 16-bit ids, class ids in shared memory, class arrays global
 constexpr int kWideMaxN = 131072;            // 32-bit ids: 4 words per thread at 1024 threads
 
-// EXACT: the search leaves exact parents by position (feed.ppos), the
-// earlier-than masks (feed.emask, when given) and the check's initial keys;
-// otherwise parent (nullable) receives p(v) for every vertex.
-template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, bool SPLIT, bool EXACT>
+template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, bool SPLIT = false>
 __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
                                                          int count, int32_t *__restrict__ order,
                                                          int32_t *__restrict__ pos, int32_t *__restrict__ parent,
-                                                         unsigned char *gstate, size_t gstate_stride,
-                                                         int *work_counter, CheckFeed feed) {
+                                                         int pmode, unsigned char *gstate, size_t gstate_stride,
+                                                         int *work_counter, unsigned long long *keys) {
     extern __shared__ __align__(16) unsigned char smem[];
     LexScalars *sc = reinterpret_cast<LexScalars *>(smem);
     unsigned char *free_smem = smem + kLexScalarBytes;
-    if (feed.keys && blockIdx.x == 0 && threadIdx.x == 0) {   // the check's block counter and error word
-        feed.keys[count] = 0ull;
-        feed.keys[count + 1] = 0ull;
+    if (keys && blockIdx.x == 0 && threadIdx.x == 0) {   // the check's CTA counter and error word
+        keys[count] = 0ull;
+        keys[count + 1] = 0ull;
     }
     for (;;) {
         if (threadIdx.x == 0) sc->next_graph = count == 1 ? (int)blockIdx.x : atomicAdd(work_counter, 1);
@@ -39,10 +36,13 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
         const int n = d.n;
         LexState<Id> st;
         unsigned char *p = free_smem;
-        if (SPLIT) {
+        // where the state lives is fixed per variant at compile time, so every
+        // state access compiles to a shared- or a global-memory instruction
+        // (a runtime choice leaves generic loads, stores and atomics)
+        if constexpr (SPLIT) {
             st = lex_state_carve_split<Id>(p, gstate + (size_t)blockIdx.x * gstate_stride, n);
             p += lex_split_smem_bytes<Id>(n);
-        } else if (gstate) {
+        } else if constexpr (sizeof(Id) == 4) {   // 32-bit ids: the whole state in the workspace
             st = lex_state_carve<Id>(gstate + (size_t)blockIdx.x * gstate_stride, n);
         } else {
             st = lex_state_carve<Id>(p, n);
@@ -63,20 +63,9 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
             stride = wn;
             __syncthreads();
         }
-        if (EXACT) {
-            if (threadIdx.x == 0) {
-                sc->co.cpar = feed.cpar + d.vbase;
-                sc->co.emask = feed.emask ? feed.emask + d.ebase : nullptr;
-                sc->co.estride = mask_stride(n);
-                if (feed.keys) feed.keys[gi] = ~0ull;   // "no violation"
-            }
-            __syncthreads();
-            lexbfs_cta<Id, T, WPT, LPW, true>(rows, stride, n, st, sc, order + d.obase,
-                                              pos ? pos + d.vbase : nullptr, feed.ppos + d.vbase);
-        } else {
-            lexbfs_cta<Id, T, WPT, LPW, false>(rows, stride, n, st, sc, order + d.obase,
-                                               pos ? pos + d.vbase : nullptr, parent ? parent + d.vbase : nullptr);
-        }
+        if (keys && threadIdx.x == 0) keys[gi] = ~0ull;   // "no violation"
+        lexbfs_cta<Id, T, WPT, LPW>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr,
+                                    parent ? parent + d.vbase : nullptr, pmode);
         __syncthreads();
         if (count == 1) break;
     }
@@ -85,14 +74,13 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
 template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, bool SPLIT = false>
 int launch_variant(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                    int32_t *order, int32_t *pos, int32_t *parent, int pmode, void *gstate,
-                   int *work_counter, cudaStream_t stream, const CheckFeed &feed) {
-    auto kern = pmode == kParentExact ? lexbfs_dense_kernel<Id, T, WPT, LPW, ROWS_SMEM, SPLIT, true>
-                                      : lexbfs_dense_kernel<Id, T, WPT, LPW, ROWS_SMEM, SPLIT, false>;
+                   int *work_counter, cudaStream_t stream, unsigned long long *keys) {
+    auto kern = lexbfs_dense_kernel<Id, T, WPT, LPW, ROWS_SMEM, SPLIT>;
     CG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes));
     if (count > 1) CG_CUDA_TRY(cudaMemsetAsync(work_counter, 0, sizeof(int), stream));
-    kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, single, count, order, pos, parent,
+    kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, single, count, order, pos, parent, pmode,
                                                static_cast<unsigned char *>(gstate), plan.gstate_bytes,
-                                               work_counter, feed);
+                                               work_counter, keys);
     CG_LAUNCH_CHECK("lexbfs_dense_kernel");
     return CG_OK;
 }
@@ -143,15 +131,12 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
 
 int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                         int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
-                        cudaStream_t stream, int parent_mode, const CheckFeed *feed) {
+                        cudaStream_t stream, int parent_mode, unsigned long long *keys) {
     if (count <= 0) return CG_OK;
-    if (parent_mode == kParentExact && (!feed || !feed->cpar || !feed->ppos))
-        return set_error(CG_EINVAL, "exact parents need the per-class and by-position parent buffers");
     ctas = std::max(1, std::min(ctas, count));
-    const CheckFeed fd = feed ? *feed : CheckFeed{};
     auto go = [&](auto launch, void *gs) {
         return launch(plan, descs, single, count, ctas, order, pos, parent, parent_mode, gs, work_counter, stream,
-                      fd);
+                      keys);
     };
     if (plan.split_state) return go(launch_variant<uint16_t, 1024, 2, 1, false, true>, gstate);
     if (plan.wide_ids) return go(launch_variant<uint32_t, 1024, 4, 1, false>, gstate);

@@ -34,16 +34,12 @@
 //   * parents: p(y) of the perfect-elimination check (Section 5.2), y's
 //     neighbour with the largest order index below its own, is the last pivot
 //     that moved y.  kParentMoves stores it for every moved vertex (one store
-//     per edge; the one-CTA fused test wants all parents).  kParentExact
-//     stores one value per step, the pivot's own parent: all members of a
-//     class share one label and so one latest numbered neighbour, kept per
-//     class in `cpar` (set to the pivot when a class is split off or moves
-//     whole).  A pivot chosen among the moved vertices has the current pivot
-//     as parent; one chosen from the top class that lost no member shares the
-//     current pivot's parent; one chosen from the next class reads cpar;
-//   * for the check, kParentExact also writes the parents by position and,
-//     every 32 steps, the numbered bitmask as the "earlier-than" mask of the
-//     next 32 positions (E_b = the vertices numbered before position 32 b);
+//     per edge; the one-CTA fused test wants all parents).  kParentPivots
+//     stores one value per step, by position (parent[i] = p(order[i])): a
+//     pivot chosen among the moved vertices has the current pivot as parent;
+//     one chosen from the top class that lost no member shares the current
+//     pivot's label and so its parent; one chosen from the next class gets
+//     kParentUnresolved and the check's preparation finds its parent;
 //   * the graph's rows are bulk-prefetched into L2 when the CTA starts.
 #pragma once
 #include "common.cuh"
@@ -76,25 +72,17 @@ struct LexState {
     uint32_t *numbered;             // [ceil(n/32)] bit v set once v is visited
 };
 
-// What the search leaves for the check in exact-parent mode (per graph; kept
-// in shared memory so the hot loop holds no extra registers).
-struct LexCheckOut {
-    int32_t *cpar;       // [n] parent shared by the members of each class (global scratch)
-    uint32_t *emask;     // earlier-than masks, row b (E_b) at b * estride words, or null
-    int estride;
-};
-
 struct LexScalars {
     int free_top;
     int next_graph;
     unsigned front_min[2];
     unsigned second_min[2];
     unsigned red[32];
-    LexCheckOut co;
 };
 
 constexpr unsigned kNoVertex = 0xFFFFFFFFu;
 
+// How lexbfs_cta records parents (when given a parent array).
 
 template <typename Id>
 __host__ __device__ inline size_t lex_state_bytes(int n) {
@@ -156,28 +144,25 @@ __device__ inline LexState<Id> lex_state_carve_split(unsigned char *smem, unsign
     return s;
 }
 
-// Word w of row x as stored (0 for w >= wn).  No arithmetic touches the
-// loaded value here, so a warp does not wait for it until the word is used.
-__device__ __forceinline__ uint32_t row_word_raw(const uint32_t *__restrict__ rows, int stride, int x, int w,
-                                                 int wn) {
-    uint32_t v = 0u;
-    if (w < wn) v = rows[(size_t)x * stride + w];
-    return v;
+// Word w of row x, padding bits cleared.
+__device__ __forceinline__ uint32_t row_word(const uint32_t *__restrict__ rows, int stride, int x, int w,
+                                             int wn, uint32_t lastmask) {
+    uint32_t v = rows[(size_t)x * stride + w];
+    return w == wn - 1 ? (v & lastmask) : v;
 }
 
 // One CTA computes the LexBFS order of one graph.  rows/stride address the
 // adjacency (global memory, or a compact shared-memory copy).  parent may be
 // null; otherwise it receives p(v) (-1 when v has no earlier neighbour):
-// without EXACT as parent[v], stored for every moved vertex; with EXACT as
-// parent[i] = p(order[i]), once per step, from the per-class parents of
-// sc->co (set by the caller before the call; sc->co.emask, when non-null,
-// receives the earlier-than masks).  lpw >= LPW threads share each row word
-// (thread t takes bit slice t % lpw of word t / lpw + k * T / lpw), which
-// shortens the serial bit loop; lpw grows while T / lpw still covers the row.
-template <typename Id, int T, int WPT, int LPW, bool EXACT = false>
+// under kParentMoves as parent[v], under kParentPivots as parent[i] =
+// p(order[i]) or kParentUnresolved.  lpw >= LPW threads
+// share each row word (thread t takes bit slice t % lpw of word t / lpw +
+// k * T / lpw), which shortens the serial bit loop; lpw grows while T / lpw
+// still covers the row.
+template <typename Id, int T, int WPT, int LPW>
 __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n, LexState<Id> st,
                            LexScalars *sc, int32_t *__restrict__ order, int32_t *__restrict__ pos,
-                           int32_t *__restrict__ parent) {
+                           int32_t *__restrict__ parent, int pmode = kParentMoves) {
     using Tr = IdTraits<Id>;
     using Sz = typename Tr::Sz;
     const Id kNumbered = (Id)~(Id)0;
@@ -199,14 +184,11 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
 
     for (int v = t; v < n; v += T) {
         st.cls[v] = 0;
-        if (!EXACT && parent) parent[v] = -1;
+        if (parent && pmode == kParentMoves) parent[v] = -1;
     }
     for (int k = t; k < n - 1; k += T) st.freel[k] = (Id)(k + 1);
     for (int w = t; w < wn; w += T) st.numbered[w] = 0u;
-    if (EXACT && sc->co.emask)   // E_0: nothing precedes position 0
-        for (int w = t; w < wn; w += T) sc->co.emask[w] = 0u;
     if (t == 0) {
-        if (EXACT) sc->co.cpar[0] = -1;
         st.sz[0] = (Sz)n;
         st.cnext[HEAD] = 0;
         st.cprev[0] = HEAD;
@@ -215,21 +197,18 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
         sc->front_min[0] = sc->front_min[1] = kNoVertex;
         sc->second_min[0] = sc->second_min[1] = kNoVertex;
     }
-    // row_ld: the pivot row's words as loaded (masked only where used, in
-    // phase S after the relabel pass, so the load overlaps phase A, barrier B
-    // and the relabel pass); row_prev: the previous pivot's unnumbered
-    // neighbours (this thread's bits), relabelled in the next step
-    uint32_t row_ld[WPT], row_prev[WPT], amask[WPT];
+    uint32_t row_cur[WPT], row_prev[WPT], row_nxt[WPT], amask[WPT];
     int x = 0;
 #pragma unroll
     for (int k = 0; k < WPT; ++k) {
         const int w = k * kGroups + wt;
-        row_ld[k] = row_word_raw(rows, stride, x, w, wn);
+        row_cur[k] = w < wn ? row_word(rows, stride, x, w, wn, lastmask) & part : 0u;
         row_prev[k] = 0u;
+        row_nxt[k] = 0u;
         amask[k] = 0u;
     }
     Id pending_free = kNone;
-    int par_x = -1;   // p(x) of the current pivot (thread 0)
+    int par_x = -1;   // p(x) of the current pivot (thread 0, kParentPivots)
     __syncthreads();
 
     for (int i = 0; i < n; ++i) {
@@ -237,8 +216,6 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
         const Id f = st.cnext[HEAD];
         const Id g = st.cnext[f];
         const Sz fsz = st.sz[f] & Tr::kMask;  // still counts x
-        int cpar_g = -1;   // g's parent, read early; used only when no member of g moves this step
-        if (EXACT && t == 0 && g != kNone) cpar_g = sc->co.cpar[g];
 
         // ---- phase S: deferred relabel, number x, split by N(x)
         if (t == 0) {
@@ -249,7 +226,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             }
             order[i] = x;
             if (pos) pos[x] = i;
-            if (EXACT && parent) parent[i] = par_x;
+            if (parent && pmode == kParentPivots) parent[i] = par_x;
         }
 #pragma unroll
         for (int k = 0; k < WPT; ++k) {
@@ -258,6 +235,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             if (w < wn) {
                 const uint32_t prev = row_prev[k];
                 uint32_t nb = st.numbered[w];
+                const uint32_t cur = row_cur[k] & ~nb;  // unnumbered neighbours of x
                 // relabel pass: vertices moved by the previous pivot take their new class
                 uint32_t bits = prev;
                 while (bits) {
@@ -265,8 +243,6 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                     bits &= bits - 1;
                     st.cls[y] = st.child[st.cls[y]];
                 }
-                // unnumbered neighbours of x in this thread's bits (first use of the row)
-                const uint32_t cur = row_ld[k] & part & (w == wn - 1 ? lastmask : 0xFFFFFFFFu) & ~nb;
                 // split pass: count moved members per class; a lane's first moved
                 // member of the top class (or of the next one) is its pivot candidate
                 bits = cur;
@@ -286,13 +262,13 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                         atomicMin(&sc->second_min[slot], (unsigned)y);
                         g_done = true;
                     }
-                    if (!EXACT && parent) parent[y] = x;
+                    if (parent && pmode == kParentMoves) parent[y] = x;
                 }
                 if (w == (x >> 5) && ((part >> (x & 31)) & 1u)) {
                     st.cls[x] = kNumbered;
                     st.numbered[w] = nb | (1u << (x & 31));
                 }
-                row_prev[k] = cur;
+                row_cur[k] = cur;
             }
             amask[k] = am;
         }
@@ -320,13 +296,15 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             mode = 2;
             target = g;
         }
+        // a moved pivot's parent is x; one from f (mode 1) shares x's label and parent
+        if (t == 0) par_x = mode == 0 ? x : (mode == 1 ? par_x : kParentUnresolved);
         if (mode == 0) {
 #pragma unroll
-            for (int k = 0; k < WPT; ++k) row_ld[k] = row_word_raw(rows, stride, (int)xn, k * kGroups + wt, wn);
+            for (int k = 0; k < WPT; ++k) {
+                const int w = k * kGroups + wt;
+                row_nxt[k] = w < wn ? row_word(rows, stride, (int)xn, w, wn, lastmask) & part : 0u;
+            }
         }
-        // a moved pivot's parent is x; one from f (mode 1) shares x's label and
-        // parent; one from g (mode 2) has g's
-        if (EXACT && t == 0) par_x = mode == 0 ? (int)x : (mode == 2 ? cpar_g : par_x);
 
         // ---- phase A: allocate / link split classes
 #pragma unroll
@@ -343,7 +321,6 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                 if (mv == size) {
                     st.child[c] = c;
                     st.sz[c] = size;
-                    if (EXACT) sc->co.cpar[c] = x;
                     if (fempty && c == g) {
                         st.cnext[HEAD] = g;
                         st.cprev[g] = HEAD;
@@ -353,7 +330,6 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                     const Id cn = st.freel[idx];
                     st.child[c] = cn;
                     st.sz[cn] = mv;
-                    if (EXACT) sc->co.cpar[cn] = x;
                     st.sz[c] = size - mv;
                     Id p = st.cprev[c];
                     if (fempty && p == f) p = HEAD;
@@ -376,15 +352,6 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             sc->front_min[slot ^ 1] = kNoVertex;
             sc->second_min[slot ^ 1] = kNoVertex;
         }
-        // every 32 steps the last warp saves the numbered set as the next
-        // earlier-than mask (numbered is not written again before barrier B)
-        if (EXACT && (i & 31) == 31 && i + 1 < n && t >= T - 32) {
-            uint32_t *E = sc->co.emask;
-            if (E) {
-                E += (size_t)((i + 1) >> 5) * sc->co.estride;
-                for (int w = t - (T - 32); w < wn; w += 32) E[w] = st.numbered[w];
-            }
-        }
         // class scan for the next pivot, overlapping phase A (cls is not written there)
         if (mode == 1 || mode == 2) {
             unsigned best = kNoVertex;
@@ -402,9 +369,17 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             const unsigned r = (t & 31) < (T / 32) ? sc->red[t & 31] : kNoVertex;
             xn = __reduce_min_sync(0xFFFFFFFFu, r);
 #pragma unroll
-            for (int k = 0; k < WPT; ++k) row_ld[k] = row_word_raw(rows, stride, (int)xn, k * kGroups + wt, wn);
+            for (int k = 0; k < WPT; ++k) {
+                const int w = k * kGroups + wt;
+                row_nxt[k] = w < wn ? row_word(rows, stride, (int)xn, w, wn, lastmask) & part : 0u;
+            }
         }
         x = (int)xn;
+#pragma unroll
+        for (int k = 0; k < WPT; ++k) {
+            row_prev[k] = row_cur[k];
+            row_cur[k] = row_nxt[k];
+        }
     }
 }
 

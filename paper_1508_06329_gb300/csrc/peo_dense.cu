@@ -33,7 +33,7 @@ constexpr int kRC = 8;    // row words per lane held in registers (256 words = 8
 // "Earlier-than" masks: for each group b of 32 positions, E_b has bit u set
 // iff pos(u) < 32 b.  ceil(n/32) rows of mask_stride(n) words per graph at
 // emask + ebase, row b = E_b.
-constexpr int kMaskRows = 32;         // rows b per mask tile
+constexpr int kMaskRows = 8;          // rows b per mask tile
 constexpr int kScan = 32;             // positions a prep thread scans for p(v)
 
 // (chordal, v, p, u) from a graph's key (pos(v*) << 32 | u*, or ~0 when chordal).
@@ -250,6 +250,51 @@ __global__ void order_check_kernel(int n, const int32_t *__restrict__ order, int
     }
 }
 
+// Blocks [0, mask_blocks) of a launch build a graph's earlier-than masks E_b
+// from pos: one warp per tile of 32 words w (a lane per word, holding the
+// position groups pos(u) / 32 of its 32 vertices) by kMaskRows rows b, so the
+// stores of a row are coalesced.
+__device__ void build_mask_tiles(const DenseDesc &d, const int32_t *__restrict__ pos_g, uint32_t *__restrict__ emask,
+                                 int mask_blocks) {
+    const int n = d.n;
+    const int wn = (n + 31) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int wcols = (wn + 31) >> 5, brows = (wn + kMaskRows - 1) / kMaskRows;
+    const int64_t tiles = (int64_t)wcols * brows;
+    uint32_t *E = emask + d.ebase;
+    const int es = mask_stride(n);
+    for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < tiles;
+         tile += ((int64_t)mask_blocks * blockDim.x) >> 5) {
+        const int wc = (int)(tile % wcols), br = (int)(tile / wcols);
+        const int w = (wc << 5) + lane;
+        uint32_t grp[32];   // position group of vertex 32 w + k (0xFFFFFFFF past n: never earlier)
+        if (w < wn && (w << 5) + 32 <= n && ((reinterpret_cast<uintptr_t>(pos_g) & 15) == 0)) {
+            const int4 *q = reinterpret_cast<const int4 *>(pos_g + (w << 5));
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int4 t4 = __ldg(q + k);
+                grp[4 * k] = (uint32_t)t4.x >> 5;
+                grp[4 * k + 1] = (uint32_t)t4.y >> 5;
+                grp[4 * k + 2] = (uint32_t)t4.z >> 5;
+                grp[4 * k + 3] = (uint32_t)t4.w >> 5;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const int u = (w << 5) + k;
+                grp[k] = (w < wn && u < n) ? (uint32_t)__ldg(pos_g + u) >> 5 : 0xFFFFFFFFu;
+            }
+        }
+        const int b0 = br * kMaskRows, b1 = min(b0 + kMaskRows, wn);
+        for (int b = b0; b < b1; ++b) {
+            uint32_t word = 0u;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) word |= (grp[k] < (uint32_t)b ? 1u : 0u) << k;
+            if (w < wn) E[(size_t)b * es + w] = word;
+        }
+    }
+}
+
 // The check's preparation, one launch per bucket of graphs (blockIdx.y =
 // graph): blocks [0, mask_blocks) build E_b, one warp per tile of 32 words w
 // (a lane per word, holding the position groups pos(u) / 32 of its 32
@@ -270,44 +315,9 @@ __global__ void peo_prep_kernel(const DenseDesc *__restrict__ descs, DenseDesc s
     }
     const DenseDesc d = descs ? descs[blockIdx.y] : single;
     const int n = d.n;
-    const int wn = (n + 31) >> 5;
     const int32_t *pos_g = pos + d.vbase;
     if ((int)blockIdx.x < mask_blocks) {
-        const int lane = threadIdx.x & 31;
-        const int wcols = (wn + 31) >> 5, brows = (wn + kMaskRows - 1) / kMaskRows;
-        const int64_t tiles = (int64_t)wcols * brows;
-        uint32_t *E = emask + d.ebase;
-        const int es = mask_stride(n);
-        for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < tiles;
-             tile += ((int64_t)mask_blocks * blockDim.x) >> 5) {
-            const int wc = (int)(tile % wcols), br = (int)(tile / wcols);
-            const int w = (wc << 5) + lane;
-            uint32_t grp[32];   // position group of vertex 32 w + k (0xFFFFFFFF past n: never earlier)
-            if (w < wn && (w << 5) + 32 <= n && ((reinterpret_cast<uintptr_t>(pos_g) & 15) == 0)) {
-                const int4 *q = reinterpret_cast<const int4 *>(pos_g + (w << 5));
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int4 t4 = __ldg(q + k);
-                    grp[4 * k] = (uint32_t)t4.x >> 5;
-                    grp[4 * k + 1] = (uint32_t)t4.y >> 5;
-                    grp[4 * k + 2] = (uint32_t)t4.z >> 5;
-                    grp[4 * k + 3] = (uint32_t)t4.w >> 5;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const int u = (w << 5) + k;
-                    grp[k] = (w < wn && u < n) ? (uint32_t)__ldg(pos_g + u) >> 5 : 0xFFFFFFFFu;
-                }
-            }
-            const int b0 = br * kMaskRows, b1 = min(b0 + kMaskRows, wn);
-            for (int b = b0; b < b1; ++b) {
-                uint32_t word = 0u;
-#pragma unroll
-                for (int k = 0; k < 32; ++k) word |= (grp[k] < (uint32_t)b ? 1u : 0u) << k;
-                if (w < wn) E[(size_t)b * es + w] = word;
-            }
-        }
+        build_mask_tiles(d, pos_g, emask, mask_blocks);
         return;
     }
     if (!PARENTS) return;
@@ -368,29 +378,7 @@ __global__ void invert_order_kernel(const DenseDesc *__restrict__ descs, DenseDe
     }
 }
 
-// ---- the check of a search's own order, positions in order (fed by the search)
-//
-// One CTA takes kSub consecutive positions s0 .. s0 + kSub - 1 of one graph
-// (blockIdx.y).  The search left p(v) by position (exact), the order, and
-// E_b for the group b = s0 / 32 (the vertices numbered before position 32 b),
-// so nothing is searched here: the CTA stages, per round of kChunkWords row
-// words, row v of each of its positions, row p(v) of the parents that are not
-// among its own vertices (for a LexBFS order p(v) is mostly the previous
-// pivot, i.e. the row staged just before) and the mask row E_b in shared
-// memory — one bulk copy each, all completing on one mbarrier — then each
-// warp tests its vertices:
-//   bad(v) = (row_v & ~row_p & E_b, without p) ∪ {u at positions 32 b ..
-//            pos(v) - 1 : u ∈ N(v), u != p, u ∉ N(p)}
-// and the first violation in order is kept by a 64-bit atomicMin of
-// (pos(v) << 32 | min bad(v)).  The last CTA to finish writes the results.
 constexpr unsigned kNoBad = 0xFFFFFFFFu;    // no bad vertex found
-constexpr int kGrpThreads = 256;
-constexpr int kSub = 16;                       // positions per CTA (2 per warp)
-constexpr int kExt = 8;                        // staged parent rows outside the CTA's own rows
-constexpr int kChunkWords = 512;               // row words staged per row and round (2 KiB)
-constexpr int kMaskSlot = kSub + kExt;         // slot of E_b
-constexpr int kSlots = kSub + kExt + 1;
-constexpr size_t kGrpSmemBytes = (size_t)kSlots * kChunkWords * sizeof(uint32_t);
 
 // (chordal, v, p, u) from a key, with the parent by position; chordal = -1
 // when the check could not complete (err != 0: 1 a bounded wait gave up, 2 an
@@ -414,169 +402,182 @@ __device__ __forceinline__ void write_result_ppos(const DenseDesc &d, unsigned l
     *out = r;
 }
 
-template <bool BULK>
-__global__ void __launch_bounds__(kGrpThreads) peo_group_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
+constexpr int kPosChunk = 4;   // uint4 loads per lane per array and pass (512 row words)
+
+__device__ __forceinline__ uint4 ldg4(const uint32_t *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+
+// ---- the check of a search's own order: one block per group of 32 positions
+//
+// Block (b, g) takes positions 32 b .. 32 b + 31 of graph g (blockIdx.y):
+//   1. it builds E_b, the vertices numbered before position 32 b, in shared
+//      memory from pos (a word per thread and pass: the pos of its 32
+//      vertices against 32 b; pos is small enough to stay in L1);
+//   2. it resolves the parents the search left open in the group
+//      (kParentUnresolved: pivots taken from the class after the top one),
+//      one vertex per warp: p(v) is the earlier neighbour with the largest
+//      position, from pos gathered over row v (row words loaded first, then
+//      one predicated load per bit position);
+//   3. each warp checks four of the positions: the lowest bit of row_v &
+//      ~row_p & E_b other than p (row v and row p loaded 128 bits per lane,
+//      E_b read from shared memory), plus the group's own earlier positions
+//      one per lane; the first violation in order is kept by an atomicMin of
+//      (pos(v) << 32 | u) and the last block writes the results.
+constexpr int kUnitThreads = 256;
+constexpr int kUnitWarps = kUnitThreads / 32;
+constexpr int kGatherWords = 16;   // row words per lane held at once by a gathering warp
+
+template <bool VEC>
+__global__ void __launch_bounds__(kUnitThreads) peo_unit_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
                                                                 int count, const int32_t *__restrict__ order,
-                                                                const int32_t *__restrict__ ppos,
-                                                                const uint32_t *__restrict__ emask,
+                                                                const int32_t *__restrict__ pos,
+                                                                int32_t *__restrict__ ppos,
                                                                 unsigned long long *__restrict__ keys,
                                                                 cg_result *__restrict__ res) {
-    extern __shared__ __align__(128) uint32_t sbuf[];   // kSlots rows of kChunkWords words
-    __shared__ __align__(8) unsigned long long bar;
-    __shared__ int s_v[32];         // vertices at the group's 32 positions (-1 past n)
-    __shared__ int s_p[kSub];       // p(v) of the CTA's positions (-1: none)
-    __shared__ int s_src[kSub];     // slot holding row p(v): j' < kSub own, kSub + e staged, -1 global
-    __shared__ int s_ext[kExt];     // vertex of each staged parent slot
-    __shared__ int s_next;
+    extern __shared__ __align__(16) uint32_t sE[];   // mask_stride(n) words
+    __shared__ int s_v[32], s_p[32];
+    __shared__ unsigned s_open;
     __shared__ bool s_last;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int gi = blockIdx.y;
     const DenseDesc d = descs ? descs[gi] : single;
     const int n = d.n;
-    const int s0 = blockIdx.x * kSub;
-    if (s0 < n) {
+    const int g0 = (int)blockIdx.x << 5;
+    if (g0 < n) {
         const int wn = (n + 31) >> 5;
         const uint32_t lastmask = (n & 31) ? ((1u << (n & 31)) - 1u) : 0xFFFFFFFFu;
-        const int gstart = s0 & ~31;
-        const int nsub = min(kSub, n - s0);
-        // order and parents come from the search; a value outside 0..n-1 (only
-        // possible if those buffers were overwritten) is reported, never used
-        if (t < 32) {
-            int v = gstart + t < n ? __ldg(order + d.obase + gstart + t) : -1;
-            if (gstart + t < n && (unsigned)v >= (unsigned)n) {
+        const int32_t *pos_g = pos + d.vbase;
+        const int32_t *ord_g = order + d.obase;
+        int32_t *pp_g = ppos + d.vbase;
+        if (warp == 0) {   // the group's vertices and parents (values outside 0..n-1 are reported)
+            int v = g0 + lane < n ? __ldg(ord_g + g0 + lane) : -1;
+            int p = g0 + lane < n ? __ldg(pp_g + g0 + lane) : -1;
+            const bool bad =
+                g0 + lane < n && ((unsigned)v >= (unsigned)n || p >= n || (p < -1 && p != kParentUnresolved));
+            if (bad) {
                 atomicOr(keys + count + 1, 2ull);
                 v = 0;
-            }
-            s_v[t] = v;
-        } else if (t < 32 + kSub) {
-            const int j = t - 32;
-            int p = j < nsub ? __ldg(ppos + d.vbase + s0 + j) : -1;
-            if (p >= n || p < -1) {
-                atomicOr(keys + count + 1, 2ull);
                 p = -1;
             }
-            s_p[j] = p;
-        } else if (t == 32 + kSub) {
-            s_next = 0;
-            if (BULK) {
-                mbar_init(&bar, 1);
-                fence_proxy_async_smem();
-            }
+            s_v[lane] = v;
+            s_p[lane] = p;
+            const unsigned open = __ballot_sync(0xFFFFFFFFu, p == kParentUnresolved);
+            if (lane == 0) s_open = open;
         }
-        __syncthreads();
-        if (t < kSub) {   // where row p(v) comes from: p precedes v, so an own row has a lower slot
-            const int p = s_p[t];
-            int src = -1;
-            if (p >= 0) {
-                for (int k = 0; k < t; ++k)
-                    if (s_v[s0 - gstart + k] == p) src = k;
-                if (src < 0) {
-                    const int e = atomicAdd(&s_next, 1);
-                    if (e < kExt) {
-                        src = kSub + e;
-                        s_ext[e] = p;
-                    }
+        // E_b from pos: bit k of word w is set iff pos(32 w + k) < 32 b
+        const bool vecpos = ((reinterpret_cast<uintptr_t>(pos_g) & 15) == 0);
+        for (int w = t; w < wn; w += kUnitThreads) {
+            uint32_t word = 0u;
+            if (vecpos && (w << 5) + 32 <= n) {
+                const int4 *q = reinterpret_cast<const int4 *>(pos_g + (w << 5));
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int4 p4 = __ldg(q + k);
+                    word |= (p4.x < g0 ? 1u : 0u) << (4 * k) | (p4.y < g0 ? 1u : 0u) << (4 * k + 1) |
+                            (p4.z < g0 ? 1u : 0u) << (4 * k + 2) | (p4.w < g0 ? 1u : 0u) << (4 * k + 3);
                 }
-            }
-            s_src[t] = src;
-        }
-        __syncthreads();
-        const int next = min(s_next, kExt);
-        const uint32_t *Eg = emask + d.ebase + (size_t)(s0 >> 5) * mask_stride(n);
-        unsigned umin[2] = {kNoBad, kNoBad};   // vertices j = warp and warp + 8
-        bool failed = false;
-        int round = 0;
-        for (int c0 = 0; c0 < wn; c0 += kChunkWords, ++round) {
-            const int cw = min(kChunkWords, wn - c0);
-            if (BULK) {
-                if (t == 0) {
-                    const uint32_t bytes = (uint32_t)((cw + 3) & ~3) * 4u;   // within the padded row (words % 4 == 0)
-                    mbar_arrive_expect_tx(&bar, bytes * (uint32_t)(nsub + next + 1));
-                    for (int j = 0; j < nsub; ++j)
-                        bulk_copy_g2s(sbuf + j * kChunkWords, d.rows + (size_t)s_v[s0 - gstart + j] * d.words + c0,
-                                      bytes, &bar);
-                    for (int e = 0; e < next; ++e)
-                        bulk_copy_g2s(sbuf + (kSub + e) * kChunkWords, d.rows + (size_t)s_ext[e] * d.words + c0, bytes,
-                                      &bar);
-                    bulk_copy_g2s(sbuf + kMaskSlot * kChunkWords, Eg + c0, bytes, &bar);
-                }
-                if (!mbar_wait_parity_bounded(&bar, round & 1)) failed = true;
             } else {
-                const int rows_used = nsub + next + 1;
-                for (int idx = t; idx < rows_used * cw; idx += kGrpThreads) {
-                    const int r = idx / cw, w = idx - r * cw;
-                    const uint32_t *src;
-                    int slot;
-                    if (r < nsub) {
-                        slot = r;
-                        src = d.rows + (size_t)s_v[s0 - gstart + r] * d.words;
-                    } else if (r < nsub + next) {
-                        slot = kSub + (r - nsub);
-                        src = d.rows + (size_t)s_ext[r - nsub] * d.words;
-                    } else {
-                        slot = kMaskSlot;
-                        src = Eg;
-                    }
-                    sbuf[slot * kChunkWords + w] = __ldg(src + c0 + w);
-                }
-                __syncthreads();
+                for (int k = 0; k < 32 && (w << 5) + k < n; ++k)
+                    word |= (__ldg(pos_g + (w << 5) + k) < g0 ? 1u : 0u) << k;
             }
-            if (__syncthreads_or(failed)) {   // a bounded wait gave up: report, do not test
-                if (t == 0) atomicOr(keys + count + 1, 1ull);
-                break;
-            }
-            const uint32_t *E = sbuf + kMaskSlot * kChunkWords;
+            sE[w] = word;
+        }
+        __syncthreads();
+        // open parents, one vertex per warp
+        unsigned open = s_open;
+        for (int r = 0; open; ++r) {
+            const int j = __ffs(open) - 1;
+            open &= open - 1;
+            if ((r % kUnitWarps) != warp) continue;
+            const int iv = g0 + j;
+            const uint32_t *rv = d.rows + (size_t)s_v[j] * d.words;
+            int best = -1;
+            for (int w0 = 0; w0 < wn; w0 += 32 * kGatherWords) {   // the row words first, then the pos loads
+                uint32_t rw[kGatherWords];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int j = warp + 8 * q;
-                if (j >= nsub || umin[q] != kNoBad) continue;   // a hit in an earlier round has a lower id
-                const int p = s_p[j];
-                if (p < 0) continue;   // no earlier neighbour: LN_v is empty
-                const uint32_t *rv = sbuf + j * kChunkWords;
-                const int src = s_src[j];
-                const uint32_t *rps = src >= 0 ? sbuf + src * kChunkWords : nullptr;
-                const uint32_t *rpg = d.rows + (size_t)p * d.words + c0;
-                // earlier groups: the lowest bit of row_v & ~row_p & E_b, p excluded
-                unsigned m = kNoBad;
-                for (int w0 = 0; w0 < cw; w0 += 32) {   // warp-uniform trip count
-                    const int w = w0 + lane;
-                    if (w < cw) {
-                        const int gw = c0 + w;
-                        uint32_t bits = rv[w] & ~(rps ? rps[w] : __ldg(rpg + w)) & E[w];
-                        if (gw == wn - 1) bits &= lastmask;
-                        if (gw == (p >> 5)) bits &= ~(1u << (p & 31));
-                        if (bits) m = (unsigned)((gw << 5) + __ffs(bits) - 1);
-                    }
-                    if (__any_sync(0xFFFFFFFFu, m != kNoBad)) break;   // later words hold higher ids
+                for (int k = 0; k < kGatherWords; ++k) {
+                    const int w = w0 + lane + 32 * k;
+                    rw[k] = w < wn ? __ldg(rv + w) : 0u;
+                    if (w == wn - 1) rw[k] &= lastmask;
                 }
-                // the group's own earlier positions 32 b .. pos(v) - 1, one per lane
-                if (gstart + lane < s0 + j) {
-                    const int u = s_v[lane];
-                    const int uw = (u >> 5) - c0;
-                    if (uw >= 0 && uw < cw && u != p) {
-                        const uint32_t bit = 1u << (u & 31);
-                        const uint32_t pw = rps ? rps[uw] : __ldg(rpg + uw);
-                        if ((rv[uw] & bit) && !(pw & bit)) m = min(m, (unsigned)u);
-                    }
+#pragma unroll
+                for (int k = 0; k < kGatherWords; ++k) {
+                    const int w = w0 + lane + 32 * k;
+                    int pu[32];
+#pragma unroll
+                    for (int b = 0; b < 32; ++b) pu[b] = (rw[k] >> b) & 1u ? __ldg(pos_g + (w << 5) + b) : -1;
+#pragma unroll
+                    for (int b = 0; b < 32; ++b)
+                        if (pu[b] < iv && pu[b] > best) best = pu[b];
                 }
-                m = __reduce_min_sync(0xFFFFFFFFu, m);
-                umin[q] = m;
             }
-            if (c0 + kChunkWords < wn) {   // the next round overwrites the staged rows
-                __syncthreads();
-                if (BULK) fence_proxy_async_smem();
+            best = __reduce_max_sync(0xFFFFFFFFu, best);
+            if (lane == 0) {   // also stored for the witness (the last block reads it after the counter)
+                const int pj = best >= 0 ? __ldg(ord_g + best) : -1;
+                s_p[j] = pj;
+                pp_g[iv] = pj;
             }
         }
-        if (lane == 0 && !failed) {
+        __syncthreads();
+        // the check, four positions per warp
+        for (int j = warp; j < 32 && g0 + j < n; j += kUnitWarps) {
+            const int i = g0 + j;
+            const int p = s_p[j];
+            if (p < 0) continue;   // no earlier neighbour: LN_v is empty
+            const uint32_t *rv = d.rows + (size_t)s_v[j] * d.words;
+            const uint32_t *rp = d.rows + (size_t)p * d.words;
+            unsigned m = kNoBad;
+            for (int c = 0; c < wn; c += 128 * kPosChunk) {
+                uint4 a[kPosChunk], b[kPosChunk];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int j = warp + 8 * q;
-                if (j < nsub && umin[q] != kNoBad)
-                    atomicMin(keys + gi, ((unsigned long long)(unsigned)(s0 + j) << 32) | umin[q]);
+                for (int it = 0; it < kPosChunk; ++it) {
+                    const int w = c + 128 * it + 4 * lane;
+                    if (w < wn) {
+                        if (VEC) {   // rows padded to 4 words: the whole uint4 is in bounds
+                            a[it] = ldg4(rv + w);
+                            b[it] = ldg4(rp + w);
+                        } else {
+                            a[it] = make_uint4(__ldg(rv + w), w + 1 < wn ? __ldg(rv + w + 1) : 0u,
+                                               w + 2 < wn ? __ldg(rv + w + 2) : 0u,
+                                               w + 3 < wn ? __ldg(rv + w + 3) : 0u);
+                            b[it] = make_uint4(__ldg(rp + w), w + 1 < wn ? __ldg(rp + w + 1) : 0u,
+                                               w + 2 < wn ? __ldg(rp + w + 2) : 0u,
+                                               w + 3 < wn ? __ldg(rp + w + 3) : 0u);
+                        }
+                    } else {
+                        a[it] = b[it] = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+#pragma unroll
+                for (int it = 0; it < kPosChunk; ++it) {   // a lane's words rise with (it, k): its first hit is its lowest
+                    const int w4 = c + 128 * it + 4 * lane;
+                    const uint4 e = w4 < wn ? *reinterpret_cast<const uint4 *>(sE + w4) : make_uint4(0u, 0u, 0u, 0u);
+                    const uint32_t aa[4] = {a[it].x, a[it].y, a[it].z, a[it].w};
+                    const uint32_t bb[4] = {b[it].x, b[it].y, b[it].z, b[it].w};
+                    const uint32_t ee[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int w = w4 + k;
+                        uint32_t bits = w < wn ? aa[k] & ~bb[k] & ee[k] : 0u;
+                        if (w == wn - 1) bits &= lastmask;
+                        if (w == (p >> 5)) bits &= ~(1u << (p & 31));
+                        if (bits && m == kNoBad) m = (unsigned)((w << 5) + __ffs(bits) - 1);
+                    }
+                }
+                if (__any_sync(0xFFFFFFFFu, m != kNoBad)) break;   // later chunks hold higher ids
             }
+            // the group's own earlier positions 32 b .. i - 1, one per lane
+            if (lane < j) {
+                const int u = s_v[lane];
+                if (u != p) {
+                    const uint32_t bit = 1u << (u & 31);
+                    if ((__ldg(rv + (u >> 5)) & bit) && !(__ldg(rp + (u >> 5)) & bit)) m = min(m, (unsigned)u);
+                }
+            }
+            m = __reduce_min_sync(0xFFFFFFFFu, m);
+            if (lane == 0 && m != kNoBad) atomicMin(keys + gi, ((unsigned long long)(unsigned)i << 32) | m);
         }
     }
-    // the last CTA to finish turns the keys into results (keys[count] counts CTAs)
+    // the last block to finish turns the keys into results (keys[count] counts blocks)
     __syncthreads();
     if (t == 0) {
         __threadfence();
@@ -586,7 +587,7 @@ __global__ void __launch_bounds__(kGrpThreads) peo_group_kernel(const DenseDesc 
     if (s_last) {
         __threadfence();
         const unsigned long long err = atomicAdd(keys + count + 1, 0ull);
-        for (int g = t; g < count; g += kGrpThreads)
+        for (int g = t; g < count; g += kUnitThreads)
             write_result_ppos(descs ? descs[g] : single, atomicAdd(keys + g, 0ull), err, order, ppos,
                               res + (descs ? descs[g].rindex : g));
     }
@@ -658,30 +659,30 @@ int peo_dense_launch(const DenseDesc *descs, DenseDesc single, int count, const 
     return CG_OK;
 }
 
-bool peo_group_bulk_ok(const DenseDesc &d) {
-    return (reinterpret_cast<uintptr_t>(d.rows) & 15) == 0 && (d.words & 3) == 0 && (d.ebase & 3) == 0;
+int peo_unit_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, bool vec, const int32_t *order,
+                    const int32_t *pos, int32_t *ppos, unsigned long long *keys, cg_result *res, cudaStream_t stream) {
+    if (count <= 0 || n_max <= 0) return set_error(CG_EINVAL, "position-ordered check needs vertices");
+    if (count > 65535) return set_error(CG_EINVAL, "too many graphs for one check launch (%d)", count);
+    const dim3 grid((unsigned)ceil_div(n_max, 32), (unsigned)count);
+    const size_t smem = (size_t)mask_stride(n_max) * sizeof(uint32_t);
+    if (vec) {
+        if (smem > 48 * 1024)
+            CG_CUDA_TRY(cudaFuncSetAttribute(peo_unit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+        peo_unit_kernel<true><<<grid, kUnitThreads, smem, stream>>>(descs, single, count, order, pos, ppos, keys, res);
+    } else {
+        if (smem > 48 * 1024)
+            CG_CUDA_TRY(cudaFuncSetAttribute(peo_unit_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+        peo_unit_kernel<false><<<grid, kUnitThreads, smem, stream>>>(descs, single, count, order, pos, ppos, keys,
+                                                                     res);
+    }
+    CG_LAUNCH_CHECK("peo_unit_kernel");
+    return CG_OK;
 }
 
-int peo_group_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, bool bulk, const int32_t *order,
-                     const int32_t *ppos, const uint32_t *emask, unsigned long long *keys, cg_result *res,
-                     cudaStream_t stream) {
-    if (count <= 0 || n_max <= 0) return set_error(CG_EINVAL, "position-ordered check needs count, n > 0");
-    if (count > 65535) return set_error(CG_EINVAL, "too many graphs for one check launch (%d)", count);
-    if ((reinterpret_cast<uintptr_t>(emask) & 15) != 0) return set_error(CG_EINVAL, "mask buffer not 16-byte aligned");
-    const dim3 grid((unsigned)ceil_div(n_max, kSub), (unsigned)count);
-    if (bulk) {
-        CG_CUDA_TRY(cudaFuncSetAttribute(peo_group_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kGrpSmemBytes));
-        peo_group_kernel<true><<<grid, kGrpThreads, kGrpSmemBytes, stream>>>(descs, single, count, order, ppos, emask,
-                                                                             keys, res);
-    } else {
-        CG_CUDA_TRY(cudaFuncSetAttribute(peo_group_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kGrpSmemBytes));
-        peo_group_kernel<false><<<grid, kGrpThreads, kGrpSmemBytes, stream>>>(descs, single, count, order, ppos,
-                                                                              emask, keys, res);
-    }
-    CG_LAUNCH_CHECK("peo_group_kernel");
-    return CG_OK;
+bool peo_rows_vec_ok(const DenseDesc &d) {
+    return (reinterpret_cast<uintptr_t>(d.rows) & 15) == 0 && (d.words & 3) == 0;
 }
 
 int finalize_launch(const DenseDesc *descs, DenseDesc single, int count, const unsigned long long *keys,
