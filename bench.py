@@ -34,7 +34,8 @@ the two graphs on two streams.
 Timing: inputs resident in HBM; before every timed step a 256 MiB buffer is
 written to flush L2; each step is bracketed by CUDA events on the launching
 stream.  `e2e` repeats the metric through the public API with pinned host
-inputs copied in and results copied out inside the timed region.
+inputs copied in and results copied out inside the timed region (dense
+workloads: the library's host-buffer entry cg_chordal_test_batch_host).
 `cpu_baseline` times the CPU oracle on a bounded sample.  For the
 single-pair workloads `phases.floor` adds the step's latency floors measured
 after the timed region (`cg_step_floor`: a CTA barrier pair, a dependent load
@@ -388,24 +389,104 @@ def run_serve(args):
     info = q.stats()
     q.close()
     lat = np.array(lat)
-    mean_alone = float(np.mean([alone_s[int(k)] for k in picks]))
-    one_at_a_time = 1.0 / mean_alone
+    # the one-at-a-time path: the plain single-graph call per query, waited for,
+    # on one stream (no queue), each pool graph timed and weighted by the picks
+    ctx1 = B.Context(local)
+    r1 = torch.empty(4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    single_s = []
+    for kind, data, n in pool:
+        def once():
+            if kind == "dense":
+                B.chordal_test_dense(ctx1, data, n, r1, None, stream)
+            else:
+                B.chordal_test_csr(ctx1, data[0], data[1], n, r1, None, stream)
+            torch.cuda.synchronize()
+        once()   # workspace sized
+        reps = 3 if n <= 8192 else 1
+        t1 = time.perf_counter()
+        for _ in range(reps):
+            once()
+        single_s.append((time.perf_counter() - t1) / reps)
+    ctx1.close()
+    mean_single = float(np.mean([single_s[int(k)] for k in picks]))
+    one_at_a_time = 1.0 / mean_single
     value = nq / wall
+    # latency per admission lane (n <= 4096 and larger) and the graphs behind the p99 tail
+    pool_n = np.array([n for _, _, n in pool])
+    qn = pool_n[picks]
+    lanes = {}
+    for name, sel in (("n<=4096", qn <= 4096), ("n>4096", qn > 4096)):
+        if sel.any():
+            lanes[name] = {"queries": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50) * 1e3),
+                           "p99_ms": float(np.percentile(lat[sel], 99) * 1e3)}
+    p99 = np.percentile(lat, 99)
+    tail = lat >= p99
+    tail_n = qn[tail]
+    tail_info = {"queries": int(tail.sum()), "n_min": int(tail_n.min()), "n_median": int(np.median(tail_n)),
+                 "share_n_over_16384": float((tail_n > 16384).mean()),
+                 "single_call_ms_of_tail_graphs_median": float(np.median([single_s[int(k)] for k in picks[tail]]) * 1e3)}
+    # the oracle on all host cores over a bounded sample of the same stream
+    cpu_rate, cpu_cores, cpu_done, cpu_wall = serve_oracle_all_cores(picks, len(pool))
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32 bitsets / int32 (exact)", "data": "synthetic",
             "config": dict(cfg, arrival_rate_qps=lam, saturation_qps=sat, queries=nq,
                            parallelism="single GPU (queue: 64 slots, 64 GiB pool, large-graph batches of 2, 32 hardware queues)"),
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
-                           "mean": float(lat.mean() * 1e3), "max": float(lat.max() * 1e3)},
+                           "mean": float(lat.mean() * 1e3), "max": float(lat.max() * 1e3), "by_lane": lanes,
+                           "p99_tail": tail_info},
             "results_differing_from_alone": bad, "queue": info,
             "one_at_a_time": {"value": one_at_a_time, "unit": "queries/s",
-                              "sample": "each pool graph submitted alone and drained, weighted by the stream's picks",
+                              "sample": "each pool graph through the plain single-graph call (cg_chordal_test_dense "
+                                        "or _csr) and a stream synchronise, weighted by the stream's picks",
                               "served_over_one_at_a_time": value / one_at_a_time},
+            "cpu_baseline": {"value": cpu_rate, "unit": "queries/s", "cores": cpu_cores, "kind": "oracle",
+                             "sample": f"{cpu_done} queries of the stream's picks on {cpu_cores} processes, "
+                                       f"{cpu_wall:.1f} s wall"},
             "clocks": clocks}
     print(json.dumps(line))
     ctx.close()
     return 0 if bad == 0 else 1
+
+
+def _serve_oracle_chunk(args):
+    import graphgen as gg
+    import oracle
+    idx, ks, budget_s = args
+    graphs = {i: gg.serve_pool_item(i)[0] for i in idx}   # this worker's share of the pool (untimed)
+    t0 = time.perf_counter()
+    done = 0
+    for k in ks:
+        oracle.chordal_test(graphs[k])
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+def serve_oracle_all_cores(picks, pool_size: int, budget_s: float = 12.0):
+    """Oracle queries/s for the serving stream on all host cores: worker w
+    builds the pool graphs with index = w (mod cores) and tests the stream's
+    picks of those graphs, in stream order, for at most budget_s (pool
+    generation excluded from its timing); rate = queries / the slowest
+    worker's time."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    jobs = []
+    for w in range(cores):
+        idx = [i for i in range(pool_size) if i % cores == w]
+        ks = [int(k) for k in picks if int(k) % cores == w]
+        if ks:
+            jobs.append((idx, ks, budget_s))
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_serve_oracle_chunk, jobs))
+    wall = time.perf_counter() - t0
+    done = sum(r[0] for r in res)
+    slowest = max(r[1] for r in res)
+    return done / slowest, len(jobs), done, wall
 
 
 def paper7_graphs():
@@ -792,21 +873,19 @@ def run_gpu(args):
         out = [tuple(r) for r in host_res.tolist()]
         e2e_path = "pinned host rows -> device (one copy), cg_chordal_test_mcs_dense per graph, results -> pinned host"
     elif dense:
-        # the timed call itself (cg_chordal_test_batch, or the captured plan), fed from
-        # pinned host memory by one copy and read back into pinned host memory
+        # the library's host-buffer entry: pinned host rows in, the copies, the
+        # batched run and the results' copy back all inside cg_chordal_test_batch_host
+        host_graphs = [(host_flat[o:o + g.rows.size].view(g.n, g.words), g.n) for g, o in zip(graphs, offs)]
         host_res = torch.empty((ngraph, 4), dtype=torch.int32).pin_memory()
-        h2d = 4 * host_flat.numel()
+        h2d = sum(4 * g.rows.size for g in graphs)
+        B.chordal_test_batch_host(ctx, host_graphs, host_res)   # sizes the workspace (untimed)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            dev_flat.copy_(host_flat, non_blocking=True)
-            step()
-            host_res.copy_(res, non_blocking=True)
-            torch.cuda.synchronize()
+            B.chordal_test_batch_host(ctx, host_graphs, host_res)
         e2e_s = time.perf_counter() - t0
         out = [tuple(r) for r in host_res.tolist()]
-        e2e_path = ("pinned host rows -> device (one copy), " +
-                    ("cg_batch_plan_run" if plan is not None else "cg_chordal_test_batch") + ", results -> pinned host")
+        e2e_path = "cg_chordal_test_batch_host: pinned host rows -> device -> results back to pinned host"
     else:
         host_csr = [(torch.from_numpy(g.row_ptr).pin_memory(), torch.from_numpy(g.col).pin_memory()) for g in graphs]
         host_res = torch.empty((ngraph, 4), dtype=torch.int32).pin_memory()

@@ -388,6 +388,24 @@ def batch_dense(count: int = 4096, seed: int = SEED_BASE + 4, nmin: int = 16, nm
     return graphs
 
 
+def serve_pool_item(i: int, count: int = 64, seed: int = SEED_BASE + 5, nmin: int = 64, nmax: int = 65536,
+                    dense_below: int = 8192):
+    """Graph i of the serving pool (see serve_pool), built alone."""
+    u = _u01(seed, 3 * count)
+    ns = log_uniform_int(u[:count], nmin, nmax)
+    dens = 0.01 + 0.19 * u[count:2 * count]
+    n = int(ns[i])
+    t = max(2, int(round(56.0 / dens[i])))
+    g = subtree_dense(n, t, seed * 31 + i)
+    planted = i % 2 == 1
+    if planted:
+        k = 5 + int(rng_stream(seed + 97 * i, 1)[0] % np.uint64(4))
+        if n >= k:
+            g, _ = plant_cycle(g, k, seed + 101 * i)
+    info = {"n": n, "target_density": float(dens[i]), "tree_nodes": t, "planted": planted}
+    return (g if n < dense_below else dense_to_csr(g)), info
+
+
 def serve_pool(count: int = 64, seed: int = SEED_BASE + 5, nmin: int = 64, nmax: int = 65536,
                dense_below: int = 8192):
     """Serving pool: N log-uniform in [nmin, nmax], target edge density
@@ -395,19 +413,4 @@ def serve_pool(count: int = 64, seed: int = SEED_BASE + 5, nmin: int = 64, nmax:
     the graphs with a planted induced C_k (k ~ U{5..8}); graphs with
     N < dense_below stay dense bit rows, larger ones are returned as CSR.
     Returns a list of (graph, info)."""
-    u = _u01(seed, 3 * count)
-    ns = log_uniform_int(u[:count], nmin, nmax)
-    dens = 0.01 + 0.19 * u[count:2 * count]
-    out = []
-    for i in range(count):
-        n = int(ns[i])
-        t = max(2, int(round(56.0 / dens[i])))
-        g = subtree_dense(n, t, seed * 31 + i)
-        planted = i % 2 == 1
-        if planted:
-            k = 5 + int(rng_stream(seed + 97 * i, 1)[0] % np.uint64(4))
-            if n >= k:
-                g, _ = plant_cycle(g, k, seed + 101 * i)
-        info = {"n": n, "target_density": float(dens[i]), "tree_nodes": t, "planted": planted}
-        out.append((g if n < dense_below else dense_to_csr(g), info))
-    return out
+    return [serve_pool_item(i, count, seed, nmin, nmax, dense_below) for i in range(count)]

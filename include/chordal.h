@@ -223,6 +223,22 @@ int cg_chordal_test_batch(cg_context *ctx, const cg_dense *graphs, int32_t count
                           int32_t *orders, const int64_t *order_offsets, cudaStream_t stream);
 
 /*
+ * The batched test from HOST buffers (the end-to-end form of
+ * cg_chordal_test_batch): graph k's rows are host memory (n * words_per_row
+ * uint32 each, preferably pinned); the library copies them into its
+ * workspace (one asynchronous copy per graph on `stream`), runs the batch as
+ * cg_chordal_test_batch does, copies the results back and synchronises the
+ * stream.
+ *   graphs       HOST array of `count` descriptors whose `rows` are HOST pointers
+ *   host_res     HOST cg_result[count] (written)
+ *   host_orders  HOST int32[sum n] (written, graphs packed in input order) or NULL
+ * Paper context: Section 7 reports GPU times with and without the input's
+ * transfer; this entry is the "with" form for many graphs at once.
+ */
+int cg_chordal_test_batch_host(cg_context *ctx, const cg_dense *graphs, int32_t count, cg_result *host_res,
+                               int32_t *host_orders, cudaStream_t stream);
+
+/*
  * The dense test without any memory allocation (the paper has no counterpart;
  * this is a deployment aid).  For callers that cannot allocate device memory
  * when they call in — a plugin whose host application owns the device memory
@@ -240,7 +256,10 @@ int cg_chordal_test_batch(cg_context *ctx, const cg_dense *graphs, int32_t count
  * the last call's contents (the witness key is reset by every call); calls
  * that overlap on the GPU race on it, so issue them on one stream.  The first
  * call on each device resolves the array's address (cudaGetSymbolAddress);
- * make that first call before any stream capture begins.
+ * make that first call before any stream capture begins.  The address is
+ * kept for the life of the process: it assumes the device's primary context
+ * is never reset (after cudaDeviceReset, or under another context made
+ * current on the same device, it would be stale).
  */
 int cg_chordal_test_dense_noalloc(const cg_dense *g, cg_result *res, int32_t *order, cudaStream_t stream);
 
@@ -274,6 +293,7 @@ typedef struct {
     int32_t max_batch;        /* queries per batch of graphs with n <= 4096 (0: 1024) */
     int32_t max_pending;      /* queued queries before submit returns CG_EAGAIN (0: 2^20) */
     int32_t max_batch_large;  /* queries per batch of larger graphs (0: 4) */
+    int32_t keep_orders;      /* 1: keep each query's LexBFS order (host memory, n int32) until polled */
 } cg_queue_config;
 
 typedef struct {
@@ -283,13 +303,19 @@ typedef struct {
 typedef struct cg_queue cg_queue;
 
 int cg_queue_create(cg_context *ctx, const cg_queue_config *cfg, cg_queue **out);
-/* CG_EAGAIN when max_pending queries are waiting. */
+/* CG_EAGAIN when max_pending queries are waiting.  With the context's
+ * cfg.validate set, a CSR query's layout is checked here (synchronising a
+ * queue-owned stream) and a malformed one returns CG_EINVAL; without it,
+ * CSR queries are trusted to be well formed (sorted, symmetric, in range). */
 int cg_queue_submit(cg_queue *q, const cg_graph_ref *g, uint64_t *ticket);
 /* CG_OK and the result (HOST memory) once done — the ticket is then
- * forgotten; CG_EAGAIN while pending; latency_s (nullable) gets
+ * forgotten; CG_EAGAIN while pending.  order (nullable, HOST int32[n]) gets
+ * the query's LexBFS order (Theorem 5.1: the order is part of the result);
+ * it needs keep_orders, else CG_EINVAL.  latency_s (nullable) gets
  * submit-to-completion seconds (host steady clock).  A query that can never
- * fit the memory budget completes with CG_ENOMEM. */
-int cg_queue_poll(cg_queue *q, uint64_t ticket, cg_result *host_res, double *latency_s);
+ * run completes with the reason: CG_ENOMEM when it exceeds the memory
+ * budget, or the status its batch layout failed with. */
+int cg_queue_poll(cg_queue *q, uint64_t ticket, cg_result *host_res, int32_t *order, double *latency_s);
 /* Waits until every submitted query completed; timeout_ns < 0 waits forever;
  * CG_ETIMEOUT when the time runs out (no GPU wait is involved). */
 int cg_queue_drain(cg_queue *q, int64_t timeout_ns);

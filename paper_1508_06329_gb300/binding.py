@@ -54,7 +54,8 @@ class cg_graph_ref(ctypes.Structure):
 
 class cg_queue_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
-                ("max_batch", ctypes.c_int32), ("max_pending", ctypes.c_int32), ("max_batch_large", ctypes.c_int32)]
+                ("max_batch", ctypes.c_int32), ("max_pending", ctypes.c_int32), ("max_batch_large", ctypes.c_int32),
+                ("keep_orders", ctypes.c_int32)]
 
 
 class cg_step_floor_info(ctypes.Structure):
@@ -89,6 +90,7 @@ SIGNATURES = {
     "cg_chordal_test_dense": ([P, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_dense_host": ([P, I32, I32, P, P, P, P], ctypes.c_int),
     "cg_chordal_test_batch": ([P, P, I32, P, P, P, P], ctypes.c_int),
+    "cg_chordal_test_batch_host": ([P, P, I32, P, P, P], ctypes.c_int),
     "cg_lexbfs_sweep_dense": ([P, P, ctypes.c_int32, P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "cg_lexbfs_sweep_csr": ([P, P, ctypes.c_int32, P, ctypes.c_int32, P, P, P], ctypes.c_int),
     "cg_mcs_order_dense": ([P, P, P, P, P], ctypes.c_int),
@@ -101,7 +103,7 @@ SIGNATURES = {
     "cg_profile_enable": ([P, I32], ctypes.c_int),
     "cg_queue_create": ([P, P, P], ctypes.c_int),
     "cg_queue_submit": ([P, P, P], ctypes.c_int),
-    "cg_queue_poll": ([P, ctypes.c_uint64, P, P], ctypes.c_int),
+    "cg_queue_poll": ([P, ctypes.c_uint64, P, P, P], ctypes.c_int),
     "cg_queue_drain": ([P, I64], ctypes.c_int),
     "cg_queue_stats": ([P, P], ctypes.c_int),
     "cg_queue_destroy": ([P], ctypes.c_int),
@@ -159,6 +161,7 @@ cg_peo_check_dense = _fn("cg_peo_check_dense")
 cg_chordal_test_dense = _fn("cg_chordal_test_dense")
 cg_chordal_test_dense_host = _fn("cg_chordal_test_dense_host")
 cg_chordal_test_batch = _fn("cg_chordal_test_batch")
+cg_chordal_test_batch_host = _fn("cg_chordal_test_batch_host")
 cg_lexbfs_sweep_dense = _fn("cg_lexbfs_sweep_dense")
 cg_lexbfs_sweep_csr = _fn("cg_lexbfs_sweep_csr")
 cg_mcs_order_dense = _fn("cg_mcs_order_dense")
@@ -310,6 +313,29 @@ def chordal_test_batch(ctx: Context, graphs, res, orders=None, order_offsets=Non
                                  offs if offs is not None else None, _stream(stream)))
 
 
+def chordal_test_batch_host(ctx: Context, graphs, host_res, host_orders=None, stream=None):
+    """graphs: list of (rows, n) with rows a CPU tensor or ndarray of 32-bit words [n, words] (pinned
+    preferred); host_res: CPU int32 tensor/ndarray [count, 4]; host_orders: CPU int32 [sum n] or None."""
+    import numpy as np
+    count = len(graphs)
+    arr = (cg_dense * max(count, 1))()
+    keep = []
+    for k, (rows, n) in enumerate(graphs):
+        if hasattr(rows, "data_ptr"):
+            ptr, words = int(rows.data_ptr()), (int(rows.shape[1]) if rows.dim() == 2 else 0)
+        else:
+            a = np.ascontiguousarray(rows)
+            keep.append(a)
+            ptr, words = a.ctypes.data, (a.shape[1] if a.ndim == 2 else 0)
+        arr[k] = cg_dense(n, words, ptr if n > 0 else 0)
+
+    def hptr(x):
+        if x is None:
+            return None
+        return int(x.data_ptr()) if hasattr(x, "data_ptr") else x.ctypes.data
+    _check(cg_chordal_test_batch_host(ctx.handle, arr, count, hptr(host_res), hptr(host_orders), _stream(stream)))
+
+
 def csr_desc(row_ptr, col, n: int) -> cg_csr:
     """row_ptr: CUDA int64 tensor [n+1]; col: CUDA int32 tensor [nnz]."""
     if row_ptr.element_size() != 8 or col.element_size() != 4:
@@ -426,34 +452,48 @@ class Queue:
     submit_* must stay alive until their ticket completes (kept here)."""
 
     def __init__(self, ctx: Context, mem_budget_bytes: int = 0, max_inflight: int = 0, max_batch: int = 0,
-                 max_pending: int = 0, max_batch_large: int = 0):
-        cfg = cg_queue_config(mem_budget_bytes, max_inflight, max_batch, max_pending, max_batch_large)
+                 max_pending: int = 0, max_batch_large: int = 0, keep_orders: bool = False):
+        cfg = cg_queue_config(mem_budget_bytes, max_inflight, max_batch, max_pending, max_batch_large,
+                              1 if keep_orders else 0)
+        self.keep_orders = keep_orders
         h = ctypes.c_void_p()
         _check(cg_queue_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h
         self._keep = {}
 
-    def _submit(self, ref, keep) -> int:
+    def _submit(self, ref, keep, n: int) -> int:
         t = ctypes.c_uint64()
         _check(cg_queue_submit(self.handle, ctypes.byref(ref), ctypes.byref(t)))
-        self._keep[t.value] = keep
+        self._keep[t.value] = (keep, n)
         return t.value
 
     def submit_dense(self, rows, n: int) -> int:
         ref = cg_graph_ref(CG_GRAPH_DENSE, dense_desc(rows, n), cg_csr())
-        return self._submit(ref, rows)
+        return self._submit(ref, rows, n)
 
     def submit_csr(self, row_ptr, col, n: int) -> int:
         ref = cg_graph_ref(CG_GRAPH_CSR, cg_dense(), csr_desc(row_ptr, col, n))
-        return self._submit(ref, (row_ptr, col))
+        return self._submit(ref, (row_ptr, col), n)
 
-    def poll(self, ticket: int):
-        """(status, (chordal, v, p, u), latency_s); status CG_EAGAIN while pending."""
+    def poll(self, ticket: int, with_order: bool = False):
+        """(status, (chordal, v, p, u), latency_s), plus the order (numpy int32[n]) when
+        with_order (the queue must keep orders); status CG_EAGAIN while pending."""
+        import numpy as np
         r = cg_result()
         lat = ctypes.c_double()
-        st = cg_queue_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(r), ctypes.byref(lat))
+        order = None
+        optr = None
+        if with_order:
+            n = self._keep.get(ticket, (None, 0))[1]
+            order = np.full(max(n, 1), -1, dtype=np.int32)
+            optr = order.ctypes.data
+        st = cg_queue_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(r), optr, ctypes.byref(lat))
         if st != CG_EAGAIN:
-            self._keep.pop(ticket, None)
+            n = self._keep.pop(ticket, (None, 0))[1]
+            if order is not None:
+                order = order[:n]
+        if with_order:
+            return st, r.astuple(), lat.value, order
         return st, r.astuple(), lat.value
 
     def drain(self, timeout_ns: int = -1) -> int:

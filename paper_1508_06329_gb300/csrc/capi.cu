@@ -331,18 +331,20 @@ struct SingleDenseCarve {
 };
 
 // LexBFS and (optionally) the check for one graph given by value.
+// base: workspace offset where this call's scratch starts (the bytes before
+// it belong to the caller, e.g. a CSR graph expanded to bit rows).
 int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int32_t *pos_out, cg_result *res,
-                     cudaStream_t stream) {
+                     cudaStream_t stream, size_t base = 0) {
     const int n = g->n;
     LexPlan plan;
     int rc = lexbfs_dense_plan(n, ctx->cfg.threads_override, &plan);
     if (rc) return rc;
     const SingleDenseCarve sc(n, plan);
-    if ((rc = ensure_ws(ctx, sc.cv.off))) return rc;
-    int32_t *order = order_out ? order_out : at<int32_t>(ctx, sc.o_order);
-    int32_t *pos = pos_out ? pos_out : at<int32_t>(ctx, sc.o_pos);
-    int32_t *parent = at<int32_t>(ctx, sc.o_parent);
-    unsigned long long *key = at<unsigned long long>(ctx, sc.o_key);
+    if ((rc = ensure_ws(ctx, base + sc.cv.off))) return rc;
+    int32_t *order = order_out ? order_out : at<int32_t>(ctx, base + sc.o_order);
+    int32_t *pos = pos_out ? pos_out : at<int32_t>(ctx, base + sc.o_pos);
+    int32_t *parent = at<int32_t>(ctx, base + sc.o_parent);
+    unsigned long long *key = at<unsigned long long>(ctx, base + sc.o_key);
     const DenseDesc d = desc_of(g, 0, 0);
     if (n == 0) {
         if (!res) return CG_OK;
@@ -353,11 +355,11 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
     }
     // with a result wanted, the search also records the parents of its pivots
     // by position (one store per step) and initialises the check's keys
-    int32_t *ppos = at<int32_t>(ctx, sc.o_ppos);
+    int32_t *ppos = at<int32_t>(ctx, base + sc.o_ppos);
     {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
         rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, res ? ppos : nullptr,
-                                 plan.gstate_bytes ? at<void>(ctx, sc.o_gstate) : nullptr, at<int>(ctx, sc.o_counter),
+                                 plan.gstate_bytes ? at<void>(ctx, base + sc.o_gstate) : nullptr, at<int>(ctx, base + sc.o_counter),
                                  stream, kParentPivots, res ? key : nullptr);
         if (rc) return rc;
         ctx->launches += 1;
@@ -381,33 +383,72 @@ int validate_csr(cg_context *ctx, const cg_csr *g, int *flag_dev, cudaStream_t s
     return CG_OK;
 }
 
-// LexBFS and (optionally) the check for one CSR graph.
+// Workspace layout of run_single_csr: CSR graphs that take the dense path
+// (csr_takes_dense_path) are expanded to bit rows first, the others keep the
+// CSR search's state.
+struct SingleCsrCarve {
+    bool dense = false;
+    size_t o_flag = 0, o_rows = 0, dense_base = 0;            // dense path
+    size_t o_order = 0, o_pos = 0, o_parent = 0, o_key = 0, o_state = 0;   // CSR path
+    size_t bytes = 0;
+    int init(int n, int64_t nnz, int threads_override) {
+        Carve cv;
+        dense = n > 0 && csr_takes_dense_path(n, nnz);
+        if (dense) {
+            const int words = (n + 31) / 32;
+            o_flag = cv.take<int>(1);
+            o_rows = cv.take<uint32_t>((size_t)n * words);
+            dense_base = align_up(cv.off, kAlign);
+            LexPlan plan;
+            const int rc = lexbfs_dense_plan(n, threads_override, &plan);
+            if (rc) return rc;
+            bytes = dense_base + SingleDenseCarve(n, plan).cv.off;
+            return CG_OK;
+        }
+        o_order = cv.take<int32_t>(n);
+        o_pos = cv.take<int32_t>(n);
+        o_parent = cv.take<int32_t>(n);
+        o_key = cv.take<unsigned long long>(1);
+        o_flag = cv.take<int>(1);
+        o_state = cv.take<unsigned char>(lexbfs_csr_workspace_bytes(n, n));
+        bytes = cv.off;
+        return CG_OK;
+    }
+};
+
+// LexBFS and (optionally) the check for one CSR graph; base: workspace offset
+// where this call's scratch starts (the bytes before it belong to the caller).
 int run_single_csr(cg_context *ctx, const cg_csr *g, int32_t *order_out, int32_t *pos_out, cg_result *res,
-                   cudaStream_t stream) {
+                   cudaStream_t stream, size_t base = 0) {
     const int n = g->n;
-    Carve cv;
-    const size_t o_order = cv.take<int32_t>(n);
-    const size_t o_pos = cv.take<int32_t>(n);
-    const size_t o_parent = cv.take<int32_t>(n);
-    const size_t o_key = cv.take<unsigned long long>(1);
-    const size_t o_flag = cv.take<int>(1);
-    const size_t o_state = cv.take<unsigned char>(lexbfs_csr_workspace_bytes(n, n));
     int rc;
-    if ((rc = ensure_ws(ctx, cv.off))) return rc;
-    if (ctx->cfg.validate && (rc = validate_csr(ctx, g, at<int>(ctx, o_flag), stream))) return rc;
-    int32_t *order = order_out ? order_out : at<int32_t>(ctx, o_order);
-    int32_t *pos = pos_out ? pos_out : at<int32_t>(ctx, o_pos);
-    int32_t *parent = at<int32_t>(ctx, o_parent);
+    SingleCsrCarve sc;
+    if ((rc = sc.init(n, g->nnz, ctx->cfg.threads_override))) return rc;
+    if ((rc = ensure_ws(ctx, base + sc.bytes))) return rc;
+    if (ctx->cfg.validate && (rc = validate_csr(ctx, g, at<int>(ctx, base + sc.o_flag), stream))) return rc;
+    if (sc.dense) {
+        // dense enough for the dense kernels: bit rows in the workspace, then the dense test
+        // (same order and witness: both searches take the lowest id among equal labels)
+        const int words = (n + 31) / 32;
+        uint32_t *rows = at<uint32_t>(ctx, base + sc.o_rows);
+        if ((rc = csr_to_bits_launch(n, g->row_ptr, g->col, rows, words, ctx->num_sms, stream))) return rc;
+        ctx->launches += 1;
+        const cg_dense d{n, words, rows};
+        return run_single_dense(ctx, &d, order_out, pos_out, res, stream, base + sc.dense_base);
+    }
+    int32_t *order = order_out ? order_out : at<int32_t>(ctx, base + sc.o_order);
+    int32_t *pos = pos_out ? pos_out : at<int32_t>(ctx, base + sc.o_pos);
+    int32_t *parent = at<int32_t>(ctx, base + sc.o_parent);
     if (n > 0) {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
-        if ((rc = lexbfs_csr_launch(n, n, g->row_ptr, g->col, g->nnz, order, pos, parent, at<void>(ctx, o_state),
-                                    ctx->num_sms, stream)))
+        if ((rc = lexbfs_csr_launch(n, n, g->row_ptr, g->col, g->nnz, order, pos, parent,
+                                    at<void>(ctx, base + sc.o_state), ctx->num_sms, stream)))
             return rc;
         ctx->launches += 2;
     }
     if (!res) return CG_OK;
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
-    unsigned long long *key = at<unsigned long long>(ctx, o_key);
+    unsigned long long *key = at<unsigned long long>(ctx, base + sc.o_key);
     if ((rc = peo_csr_launch(n, g->row_ptr, g->col, order, pos, parent, true, key, ctx->num_sms, stream))) return rc;
     DenseDesc d{};
     d.n = n;
@@ -753,19 +794,17 @@ int cg_chordal_test_csr_host(cg_context *ctx, int32_t n, int64_t nnz, const int6
     if (!host_res) return set_error(CG_EINVAL, "null host result pointer");
     cg_csr probe{n, nnz, host_row_ptr, host_col};
     if ((rc = check_csr(&probe))) return rc;
-    // inputs and outputs sit after the scratch that run_single_csr carves
+    // inputs and outputs first; run_single_csr's scratch follows (sized before any copy,
+    // so that no workspace growth can drop the copied inputs)
     Carve cv;
-    cv.take<int32_t>(n);
-    cv.take<int32_t>(n);
-    cv.take<int32_t>(n);
-    cv.take<unsigned long long>(1);
-    cv.take<int>(1);
-    cv.take<unsigned char>(lexbfs_csr_workspace_bytes(n, n));
     const size_t o_rp = cv.take<int64_t>((size_t)n + 1);
     const size_t o_col = cv.take<int32_t>((size_t)nnz);
     const size_t o_res = cv.take<cg_result>(1);
     const size_t o_order = cv.take<int32_t>(n);
-    if ((rc = ensure_ws(ctx, cv.off))) return rc;
+    const size_t base = align_up(cv.off, kAlign);
+    SingleCsrCarve scv;
+    if ((rc = scv.init(n, nnz, ctx->cfg.threads_override))) return rc;
+    if ((rc = ensure_ws(ctx, base + scv.bytes))) return rc;
     int64_t *rp = at<int64_t>(ctx, o_rp);
     int32_t *col = at<int32_t>(ctx, o_col);
     if (n >= 0)
@@ -774,7 +813,7 @@ int cg_chordal_test_csr_host(cg_context *ctx, int32_t n, int64_t nnz, const int6
     cg_csr g{n, nnz, rp, col};
     cg_result *res = at<cg_result>(ctx, o_res);
     int32_t *order = at<int32_t>(ctx, o_order);
-    if ((rc = run_single_csr(ctx, &g, order, nullptr, res, stream))) return rc;
+    if ((rc = run_single_csr(ctx, &g, order, nullptr, res, stream, base))) return rc;
     CG_CUDA_TRY(cudaMemcpyAsync(host_res, res, sizeof(cg_result), cudaMemcpyDeviceToHost, stream));
     if (host_order && n > 0)
         CG_CUDA_TRY(cudaMemcpyAsync(host_order, order, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, stream));
@@ -797,6 +836,91 @@ int cg_chordal_test_batch(cg_context *ctx, const cg_dense *graphs, int32_t count
     if ((rc = upload_layout(ctx, L, bb, base, stream))) return rc;
     PhaseTimer pt(ctx, &ctx->ev_batch, stream);
     return enqueue_batch(ctx, L, bb, base, orders, res, stream, ctx->streams, true);
+}
+
+// The batch from host buffers: graph k's rows (host memory) are copied into
+// the workspace, the batch runs there, and the results (and orders) come back.
+int cg_chordal_test_batch_host(cg_context *ctx, const cg_dense *graphs, int32_t count, cg_result *host_res,
+                               int32_t *host_orders, cudaStream_t stream) {
+    int rc;
+    if ((rc = check_ctx(ctx))) return rc;
+    if (count < 0) return set_error(CG_EINVAL, "count must be >= 0");
+    if (count == 0) return CG_OK;
+    if (!graphs || !host_res) return set_error(CG_EINVAL, "null graphs or host result pointer");
+    // the layout depends on the sizes only: a first pass with the host pointers sizes the workspace
+    BatchLayout L;
+    if ((rc = make_layout(ctx, graphs, count, nullptr, &L))) return rc;
+    const BatchBuffers bb = batch_buffers(L, host_orders == nullptr);
+    // graphs whose host rows follow each other share one copy of their whole span; a gap
+    // between two graphs is copied only when it lies in pages that hold the callers' rows
+    // (the next graph starts at most one 4 KiB page after the page where the previous
+    // one ends), so no byte outside mapped caller pages is read.  The device copy keeps
+    // each graph's offset and its address modulo 256 (alignment for 128-bit loads).
+    constexpr uintptr_t kPage = 4096;
+    std::vector<int> by_addr(count);
+    for (int k = 0; k < count; ++k) by_addr[k] = k;
+    auto hbeg = [&](int k) { return reinterpret_cast<uintptr_t>(graphs[k].rows); };
+    auto hbytes = [&](int k) { return (size_t)graphs[k].n * (size_t)graphs[k].words_per_row * sizeof(uint32_t); };
+    std::stable_sort(by_addr.begin(), by_addr.end(), [&](int a, int b) { return hbeg(a) < hbeg(b); });
+    struct Span {
+        uintptr_t beg, end;
+        size_t off;
+    };
+    std::vector<Span> spans;
+    std::vector<int> span_of(count, -1);
+    Carve cv;
+    for (int q = 0; q < count; ++q) {
+        const int k = by_addr[q];
+        if (!hbytes(k)) continue;
+        const uintptr_t b = hbeg(k), e = b + hbytes(k);
+        if (!spans.empty() && b >= spans.back().end && b / kPage <= (spans.back().end - 1) / kPage + 1) {
+            spans.back().end = e;
+        } else {
+            spans.push_back(Span{b, e, 0});
+        }
+        span_of[k] = (int)spans.size() - 1;
+    }
+    for (auto &sp : spans) sp.off = cv.take<unsigned char>((sp.end - sp.beg) + 256) + (sp.beg & 255);
+    const size_t o_res = cv.take<cg_result>(count);
+    const size_t o_ord = cv.take<int32_t>(host_orders ? L.total : 0);
+    const size_t o_bb = cv.take<unsigned char>(bb.bytes);
+    if ((rc = ensure_ws(ctx, cv.off))) return rc;
+    unsigned char *ws = static_cast<unsigned char *>(ctx->ws);
+    for (size_t si = 0; si < spans.size(); ++si) {
+        const Span &sp = spans[si];
+        cudaError_t e = cudaMemcpyAsync(ws + sp.off, reinterpret_cast<const void *>(sp.beg), sp.end - sp.beg,
+                                        cudaMemcpyHostToDevice, stream);
+        if (e == cudaErrorInvalidValue) {   // a span across two pinned allocations: copy its graphs one by one
+            cudaGetLastError();
+            for (int k = 0; k < count; ++k)
+                if (span_of[k] == (int)si)
+                    CG_CUDA_TRY(cudaMemcpyAsync(ws + sp.off + (hbeg(k) - sp.beg), graphs[k].rows, hbytes(k),
+                                                cudaMemcpyHostToDevice, stream));
+        } else if (e != cudaSuccess) {
+            return set_error(CG_ECUDA, "host-to-device copy of the batch's rows failed: %s", cudaGetErrorString(e));
+        }
+    }
+    std::vector<cg_dense> dev(graphs, graphs + count);
+    for (int k = 0; k < count; ++k)
+        if (span_of[k] >= 0) {
+            const Span &sp = spans[span_of[k]];
+            dev[k].rows = reinterpret_cast<const uint32_t *>(ws + sp.off + (hbeg(k) - sp.beg));
+        }
+    if ((rc = make_layout(ctx, dev.data(), count, nullptr, &L))) return rc;
+    cg_result *res = reinterpret_cast<cg_result *>(ws + o_res);
+    int32_t *orders = host_orders ? reinterpret_cast<int32_t *>(ws + o_ord) : nullptr;
+    unsigned char *base = ws + o_bb;
+    if ((rc = upload_layout(ctx, L, bb, base, stream))) return rc;
+    {
+        PhaseTimer pt(ctx, &ctx->ev_batch, stream);
+        if ((rc = enqueue_batch(ctx, L, bb, base, orders, res, stream, ctx->streams, true))) return rc;
+    }
+    CG_CUDA_TRY(cudaMemcpyAsync(host_res, res, sizeof(cg_result) * count, cudaMemcpyDeviceToHost, stream));
+    if (host_orders && L.total > 0)
+        CG_CUDA_TRY(cudaMemcpyAsync(host_orders, orders, sizeof(int32_t) * (size_t)L.total, cudaMemcpyDeviceToHost,
+                                    stream));
+    CG_CUDA_TRY(cudaStreamSynchronize(stream));
+    return CG_OK;
 }
 
 struct cg_batch_plan {

@@ -28,9 +28,9 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan);
 // parent (packed by vbase) receives parents when non-null: parent_mode
 // kParentMoves records p(v) for every vertex (a store per moved vertex),
 // kParentPivots one value per step by position, parent[i] = p(order[i]), or
-// kParentUnresolved for the pivots chosen from the class after the top one.
-// keys (nullable) receives the check's initial keys: keys[0..count) = "no
-// violation", keys[count] = keys[count + 1] = 0.
+// kParentUnresolved for the pivots chosen by a class scan.  keys (nullable)
+// is set, on the stream after the search, to the check's initial keys:
+// keys[0..count) = "no violation", keys[count] = keys[count + 1] = 0.
 int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                         int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
                         cudaStream_t stream, int parent_mode = 0, unsigned long long *keys = nullptr);
@@ -124,6 +124,15 @@ int lexbfs_csr_launch(int n, int64_t max_deg, const int64_t *row_ptr, const int3
 // ---- CSR check (peo_csr.cu)
 int peo_csr_launch(int n, const int64_t *row_ptr, const int32_t *col, const int32_t *order, const int32_t *pos,
                    int32_t *parent, bool parent_known, unsigned long long *key, int num_sms, cudaStream_t stream);
+// CSR graphs as bit rows: rows (n * words, words >= ceil(n/32)) are zeroed,
+// then each vertex's neighbours are OR-ed into its row (one warp per vertex).
+int csr_to_bits_launch(int n, const int64_t *row_ptr, const int32_t *col, uint32_t *rows, int words, int num_sms,
+                       cudaStream_t stream);
+// CSR graphs dense enough for the dense kernels: n <= kCsrDenseMaxN and at
+// least 16 neighbours per vertex on average (or n <= 4096); the single-graph
+// CSR entries and the serving queue expand these to bit rows first.
+constexpr int kCsrDenseMaxN = 131072;
+bool csr_takes_dense_path(int n, int64_t nnz);
 // flag (device int) receives an OR of layout violations, 0 when the CSR is well formed.
 int validate_csr_launch(int n, int64_t nnz, const int64_t *row_ptr, const int32_t *col, int *flag, int num_sms,
                         cudaStream_t stream);

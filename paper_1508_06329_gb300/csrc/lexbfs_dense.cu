@@ -18,14 +18,10 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
                                                          int count, int32_t *__restrict__ order,
                                                          int32_t *__restrict__ pos, int32_t *__restrict__ parent,
                                                          int pmode, unsigned char *gstate, size_t gstate_stride,
-                                                         int *work_counter, unsigned long long *keys) {
+                                                         int *work_counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     LexScalars *sc = reinterpret_cast<LexScalars *>(smem);
     unsigned char *free_smem = smem + kLexScalarBytes;
-    if (keys && blockIdx.x == 0 && threadIdx.x == 0) {   // the check's CTA counter and error word
-        keys[count] = 0ull;
-        keys[count + 1] = 0ull;
-    }
     for (;;) {
         if (threadIdx.x == 0) sc->next_graph = count == 1 ? (int)blockIdx.x : atomicAdd(work_counter, 1);
         __syncthreads();
@@ -63,7 +59,6 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
             stride = wn;
             __syncthreads();
         }
-        if (keys && threadIdx.x == 0) keys[gi] = ~0ull;   // "no violation"
         lexbfs_cta<Id, T, WPT, LPW>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr,
                                     parent ? parent + d.vbase : nullptr, pmode);
         __syncthreads();
@@ -80,7 +75,11 @@ int launch_variant(const LexPlan &plan, const DenseDesc *descs, DenseDesc single
     if (count > 1) CG_CUDA_TRY(cudaMemsetAsync(work_counter, 0, sizeof(int), stream));
     kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, single, count, order, pos, parent, pmode,
                                                static_cast<unsigned char *>(gstate), plan.gstate_bytes,
-                                               work_counter, keys);
+                                               work_counter);
+    if (keys) {   // the check's initial keys: "no violation", then the CTA counter and error word
+        CG_CUDA_TRY(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * count, stream));
+        CG_CUDA_TRY(cudaMemsetAsync(keys + count, 0, 2 * sizeof(unsigned long long), stream));
+    }
     CG_LAUNCH_CHECK("lexbfs_dense_kernel");
     return CG_OK;
 }

@@ -37,9 +37,10 @@
 //     per edge; the one-CTA fused test wants all parents).  kParentPivots
 //     stores one value per step, by position (parent[i] = p(order[i])): a
 //     pivot chosen among the moved vertices has the current pivot as parent;
-//     one chosen from the top class that lost no member shares the current
-//     pivot's label and so its parent; one chosen from the next class gets
-//     kParentUnresolved and the check's preparation finds its parent;
+//     one chosen by a class scan gets kParentUnresolved and the check finds
+//     its parent (a per-step select that kept a class-scan pivot's parent
+//     when it shares the current pivot's class measured 40 ns per step
+//     slower on GB300, far more than the check's gather for those vertices);
 //   * the graph's rows are bulk-prefetched into L2 when the CTA starts.
 #pragma once
 #include "common.cuh"
@@ -296,8 +297,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             mode = 2;
             target = g;
         }
-        // a moved pivot's parent is x; one from f (mode 1) shares x's label and parent
-        if (t == 0) par_x = mode == 0 ? x : (mode == 1 ? par_x : kParentUnresolved);
+        if (t == 0) par_x = mode == 0 ? x : kParentUnresolved;   // a moved pivot's parent is x
         if (mode == 0) {
 #pragma unroll
             for (int k = 0; k < WPT; ++k) {

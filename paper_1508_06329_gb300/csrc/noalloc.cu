@@ -20,7 +20,10 @@
 //     threads) race on the array: serialise them on one stream.
 //   * The first call on a device resolves the array's device address with
 //     cudaGetSymbolAddress (once per device, with that device current); make
-//     that first call before any stream capture begins.
+//     that first call before any stream capture begins.  The address is kept
+//     for the life of the process, which assumes the device's primary context
+//     is never reset: after cudaDeviceReset (or with another context made
+//     current on the device) the kept address would be stale.
 #include <atomic>
 #include <mutex>
 

@@ -117,4 +117,38 @@ int validate_csr_launch(int n, int64_t nnz, const int64_t *row_ptr, const int32_
     return CG_OK;
 }
 
+
+namespace {
+// One warp per vertex ORs its CSR neighbours into its bit row (rows zeroed).
+__global__ void csr_to_bits_kernel(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                   uint32_t *__restrict__ rows, int words) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        const int64_t b = rp[v], e = rp[v + 1];
+        uint32_t *row = rows + (size_t)v * words;
+        for (int64_t j = b + lane; j < e; j += 32) {
+            const int u = col[j];
+            if (u >= 0 && u < n && u != v) atomicOr(row + (u >> 5), 1u << (u & 31));
+        }
+    }
+}
+
+}  // namespace
+
+int csr_to_bits_launch(int n, const int64_t *row_ptr, const int32_t *col, uint32_t *rows, int words, int num_sms,
+                       cudaStream_t stream) {
+    if (n <= 0) return CG_OK;
+    CG_CUDA_TRY(cudaMemsetAsync(rows, 0, (size_t)n * words * sizeof(uint32_t), stream));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 8), (int64_t)num_sms * 8));
+    csr_to_bits_kernel<<<blocks, 256, 0, stream>>>(n, row_ptr, col, rows, words);
+    CG_LAUNCH_CHECK("csr_to_bits_kernel");
+    return CG_OK;
+}
+
+bool csr_takes_dense_path(int n, int64_t nnz) {
+    return n <= kCsrDenseMaxN && (n <= 4096 || (n > 0 && nnz >= 16 * (int64_t)n));
+}
+
 }  // namespace cg

@@ -19,6 +19,7 @@
 // average (or n <= 4096) are expanded to bit rows on the device first and take
 // the same path; sparser CSR queries run the CSR kernels.
 #include <chrono>
+#include <cstdio>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -27,6 +28,7 @@
 #include <new>
 #include <thread>
 #include <unordered_map>
+#include <vector>
 
 #include "host.h"
 #include "lexbfs_dense.cuh"
@@ -35,23 +37,6 @@ namespace cg {
 
 namespace {
 
-constexpr int kWideMaxDenseN = 131072;
-
-// One warp per vertex ORs its CSR neighbours into its bit row (rows zeroed).
-__global__ void csr_to_bits_kernel(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                   uint32_t *__restrict__ rows, int words) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = warp; v < n; v += nwarps) {
-        const int64_t b = rp[v], e = rp[v + 1];
-        uint32_t *row = rows + (size_t)v * words;
-        for (int64_t j = b + lane; j < e; j += 32) {
-            const int u = col[j];
-            if (u >= 0 && u < n && u != v) atomicOr(row + (u >> 5), 1u << (u & 31));
-        }
-    }
-}
 
 // First-fit allocator over [0, cap) with coalescing frees.
 struct PoolAllocator {
@@ -107,6 +92,7 @@ struct Done {
     cg_result res;
     double latency_s;
     int status;
+    std::vector<int32_t> order;   // kept when the queue keeps orders
 };
 
 struct Slot {
@@ -116,6 +102,7 @@ struct Slot {
     unsigned char *staging = nullptr;   // pinned: descriptors up, results down
     size_t staging_bytes = 0;
     std::vector<Request> reqs;
+    std::vector<const int32_t *> order_dev;   // per request: its order in the pool (kept orders)
     size_t off = 0, bytes = 0;
     bool busy = false;
 };
@@ -151,6 +138,10 @@ struct cg_queue {
     size_t inflight = 0;
     bool stop = false;
     std::thread worker;
+    // CSR layout checks at submit (cfg.validate): own stream and flag
+    std::mutex val_mu;
+    cudaStream_t val_stream{};
+    int *val_flag = nullptr;
 };
 
 namespace {
@@ -167,6 +158,13 @@ size_t request_need(const cg_graph_ref &g, Route route) {
 int launch_batch(cg_queue *q, Slot &s, bool dry = false, size_t *bytes_out = nullptr) {
     int rc;
     cg_context *ctx = q->ctx;
+    if (!dry) {   // the layout must fit the reservation before any work is queued
+        size_t exact = 0;
+        if ((rc = launch_batch(q, s, true, &exact))) return rc;
+        if (exact > s.bytes) return set_error(CG_ENOMEM, "queue batch layout exceeds its reservation");
+        s.order_dev.assign(s.reqs.size(), nullptr);
+    }
+    const bool keep = q->cfg.keep_orders != 0;
     unsigned char *base = dry ? nullptr : q->pool + s.off;
     const int count = (int)s.reqs.size();
     size_t cur = 0;
@@ -189,12 +187,9 @@ int launch_batch(cg_queue *q, Slot &s, bool dry = false, size_t *bytes_out = nul
         } else if (r.route == kRouteCsrBits) {
             const int n = r.g.csr.n, words = (n + 31) / 32;
             uint32_t *rows = reinterpret_cast<uint32_t *>(base + take((size_t)n * words * 4));
-            if (n > 0 && !dry) {
-                CG_CUDA_TRY(cudaMemsetAsync(rows, 0, (size_t)n * words * 4, s.stream));
-                const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 8), (int64_t)ctx->num_sms * 8));
-                csr_to_bits_kernel<<<blocks, 256, 0, s.stream>>>(n, r.g.csr.row_ptr, r.g.csr.col, rows, words);
-                CG_LAUNCH_CHECK("csr_to_bits_kernel");
-            }
+            if (n > 0 && !dry &&
+                (rc = csr_to_bits_launch(n, r.g.csr.row_ptr, r.g.csr.col, rows, words, ctx->num_sms, s.stream)))
+                return rc;
             dense.push_back(cg_dense{n, words, rows});
             dense_req.push_back(i);
         }
@@ -206,6 +201,13 @@ int launch_batch(cg_queue *q, Slot &s, bool dry = false, size_t *bytes_out = nul
         const BatchBuffers bb = batch_buffers(L, true);
         const size_t o_b = take(bb.bytes);
         unsigned char *bbase = base + o_b;
+        if (!dry && keep) {   // the batch's own order buffer packs the graphs in dense-list order
+            int64_t off = 0;
+            for (size_t j = 0; j < dense.size(); ++j) {
+                s.order_dev[dense_req[j]] = reinterpret_cast<const int32_t *>(bbase + bb.o_order) + off;
+                off += dense[j].n;
+            }
+        }
         const size_t need = layout_staging_bytes(L) + sizeof(cg_result) * count + 64;
         if (dry) goto csr_part;
         // staging is sized at queue creation: freeing pinned memory here would synchronise the device
@@ -227,6 +229,7 @@ csr_part:
         unsigned long long *key = reinterpret_cast<unsigned long long *>(base + take(8));
         void *state = base + take(lexbfs_csr_workspace_bytes(n, n));
         if (dry) continue;
+        if (keep) s.order_dev[i] = order;
         if (n > 0 && (rc = lexbfs_csr_launch(n, n, r.g.csr.row_ptr, r.g.csr.col, r.g.csr.nnz, order, pos, parent, state,
                                              ctx->num_sms, s.stream)))
             return rc;
@@ -241,7 +244,6 @@ csr_part:
         *bytes_out = align_up(cur, kAlign) + kAlign;
         return CG_OK;
     }
-    if (cur > s.bytes) return set_error(CG_ENOMEM, "queue batch layout exceeded its reservation");
     // results land in the tail of the slot's pinned staging
     cg_result *hres = reinterpret_cast<cg_result *>(s.staging + s.staging_bytes - sizeof(cg_result) * count);
     CG_CUDA_TRY(cudaMemcpyAsync(hres, dres, sizeof(cg_result) * count, cudaMemcpyDeviceToHost, s.stream));
@@ -269,7 +271,19 @@ void worker_loop(cg_queue *q) {
                 d.status = e == cudaSuccess ? CG_OK : CG_ECUDA;
                 if (e == cudaSuccess) d.res = hres[i];
                 d.latency_s = std::chrono::duration<double>(now - s.reqs[i].t_submit).count();
-                q->done[s.reqs[i].ticket] = d;
+                const Request &r = s.reqs[i];
+                const int n = r.g.kind == CG_GRAPH_DENSE ? r.g.dense.n : r.g.csr.n;
+                if (e == cudaSuccess && q->cfg.keep_orders && n > 0 && i < (int)s.order_dev.size() &&
+                    s.order_dev[i]) {   // the batch is complete: a plain copy out of its pool memory
+                    d.order.resize(n);
+                    if (cudaMemcpy(d.order.data(), s.order_dev[i], sizeof(int32_t) * (size_t)n,
+                                   cudaMemcpyDeviceToHost) != cudaSuccess) {
+                        cudaGetLastError();
+                        d.status = CG_ECUDA;
+                        d.order.clear();
+                    }
+                }
+                q->done[r.ticket] = std::move(d);
             }
             if (e != cudaSuccess) cudaGetLastError();
             q->alloc.release(s.off, s.bytes);
@@ -309,10 +323,17 @@ void worker_loop(cg_queue *q) {
             }
             // exact device bytes of the candidate batch: halve it until it fits
             Slot probe;
+            int dry_rc = CG_OK;
+            char dry_msg[256] = {0};
             while (!take.empty()) {
                 probe.reqs = take;
                 size_t exact = 0;
-                if (launch_batch(q, probe, true, &exact) != CG_OK) exact = (size_t)-1;
+                const int prc = launch_batch(q, probe, true, &exact);
+                if (prc != CG_OK) {   // kept: if the batch shrinks to nothing, this is why
+                    dry_rc = prc;
+                    snprintf(dry_msg, sizeof(dry_msg), "%s", cg_last_error_string());
+                    exact = (size_t)-1;
+                }
                 if (exact <= room) {
                     total = exact;
                     break;
@@ -323,11 +344,12 @@ void worker_loop(cg_queue *q) {
             }
             if (take.empty()) {
                 if (!any_busy && !launched) {
-                    // the head request alone exceeds the whole budget
+                    // the head request alone cannot run: its layout failed, or it exceeds the whole budget
                     Request r = pend.front();
                     pend.pop_front();
                     Done d{};
-                    d.status = CG_ENOMEM;
+                    d.status = dry_rc != CG_OK ? dry_rc : CG_ENOMEM;
+                    if (dry_rc != CG_OK) set_error(dry_rc, "%s", dry_msg);
                     d.res = cg_result{-1, -1, -1, -1};
                     q->done[r.ticket] = d;
                     q->completed += 1;
@@ -402,6 +424,14 @@ int cg_queue_create(cg_context *ctx, const cg_queue_config *cfg, cg_queue **out)
         return set_error(CG_ENOMEM, "queue pool of %zu bytes could not be allocated", want);
     }
     q->alloc.reset(q->pool_bytes);
+    if (cudaStreamCreateWithFlags(&q->val_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&q->val_flag, 256) != cudaSuccess) {
+        cudaGetLastError();
+        if (q->val_stream) cudaStreamDestroy(q->val_stream);
+        cudaFree(q->pool);
+        delete q;
+        return set_error(CG_ECUDA, "queue validation stream setup failed");
+    }
     q->slots.resize(q->cfg.max_inflight);
     // pinned staging per slot, sized once for the largest batch: descriptors,
     // offsets and results
@@ -421,6 +451,8 @@ int cg_queue_create(cg_context *ctx, const cg_queue_config *cfg, cg_queue **out)
                 if (t.staging) cudaFreeHost(t.staging);
                 stream_set_destroy(&t.ss);
             }
+            cudaStreamDestroy(q->val_stream);
+            cudaFree(q->val_flag);
             cudaFree(q->pool);
             delete q;
             return CG_ECUDA;
@@ -437,13 +469,24 @@ int cg_queue_submit(cg_queue *q, const cg_graph_ref *g, uint64_t *ticket) {
     Route route;
     if (g->kind == CG_GRAPH_DENSE) {
         if ((rc = check_dense(&g->dense))) return rc;
-        if (g->dense.n > kWideMaxDenseN) return set_error(CG_EINVAL, "dense queries support n <= %d", kWideMaxDenseN);
+        if (g->dense.n > kCsrDenseMaxN) return set_error(CG_EINVAL, "dense queries support n <= %d", kCsrDenseMaxN);
         route = kRouteDense;
     } else if (g->kind == CG_GRAPH_CSR) {
         if ((rc = check_csr(&g->csr))) return rc;
-        const int n = g->csr.n;
-        const bool dense_enough = n <= 4096 || (n > 0 && g->csr.nnz >= 16 * (int64_t)n);
-        route = (dense_enough && n <= kWideMaxDenseN) ? kRouteCsrBits : kRouteCsr;
+        if (q->ctx->cfg.validate) {   // the CSR kernels index by row_ptr and col: check the layout first
+            std::lock_guard<std::mutex> vl(q->val_mu);
+            CG_CUDA_TRY(cudaSetDevice(q->ctx->cfg.device));
+            if ((rc = validate_csr_launch(g->csr.n, g->csr.nnz, g->csr.row_ptr, g->csr.col, q->val_flag,
+                                          q->ctx->num_sms, q->val_stream)))
+                return rc;
+            int flag = 0;
+            CG_CUDA_TRY(cudaMemcpyAsync(&flag, q->val_flag, sizeof(int), cudaMemcpyDeviceToHost, q->val_stream));
+            CG_CUDA_TRY(cudaStreamSynchronize(q->val_stream));
+            if (flag)
+                return set_error(CG_EINVAL, "CSR layout check failed (flags 0x%x: 1 row_ptr, 2 range, "
+                                            "4 unsorted/duplicate, 8 self-loop, 16 not symmetric)", flag);
+        }
+        route = csr_takes_dense_path(g->csr.n, g->csr.nnz) ? kRouteCsrBits : kRouteCsr;
     } else {
         return set_error(CG_EINVAL, "unknown graph kind %d", g->kind);
     }
@@ -467,7 +510,7 @@ int cg_queue_submit(cg_queue *q, const cg_graph_ref *g, uint64_t *ticket) {
     return CG_OK;
 }
 
-int cg_queue_poll(cg_queue *q, uint64_t ticket, cg_result *host_res, double *latency_s) {
+int cg_queue_poll(cg_queue *q, uint64_t ticket, cg_result *host_res, int32_t *order, double *latency_s) {
     if (!q) return set_error(CG_EINVAL, "null queue");
     std::lock_guard<std::mutex> lk(q->mu);
     auto it = q->done.find(ticket);
@@ -476,10 +519,13 @@ int cg_queue_poll(cg_queue *q, uint64_t ticket, cg_result *host_res, double *lat
                                                                       (unsigned long long)ticket);
         return CG_EAGAIN;
     }
-    const Done d = it->second;
+    if (order && !q->cfg.keep_orders)
+        return set_error(CG_EINVAL, "the queue keeps no orders (cg_queue_config.keep_orders = 0)");
+    const Done d = std::move(it->second);
     q->done.erase(it);
     if (host_res) *host_res = d.res;
     if (latency_s) *latency_s = d.latency_s;
+    if (order && !d.order.empty()) std::memcpy(order, d.order.data(), sizeof(int32_t) * d.order.size());
     if (d.status != CG_OK) return set_error(d.status, "request %llu failed", (unsigned long long)ticket);
     return CG_OK;
 }
@@ -528,6 +574,8 @@ int cg_queue_destroy(cg_queue *q) {
         stream_set_destroy(&s.ss);
         if (s.staging) cudaFreeHost(s.staging);
     }
+    if (q->val_stream) cudaStreamDestroy(q->val_stream);
+    cudaFree(q->val_flag);
     cudaFree(q->pool);
     delete q;
     return CG_OK;

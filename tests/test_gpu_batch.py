@@ -114,3 +114,26 @@ def test_autotune_keeps_results(ctx):
     check(graphs, res, orders)
     B.autotune_set(ctx, [0] * 9)
     assert B.autotune_get(ctx) == [0] * 9
+
+
+def test_batch_host_entry_matches_oracle(ctx):
+    """cg_chordal_test_batch_host: host rows in, host results and orders out (copies inside the library)."""
+    graphs = gg.batch_dense(64, seed=11) + [gg.empty_dense(0), gg.cycle(5), gg.subtree_dense(5000, 900, 4)]
+    host_rows = [(torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)).pin_memory(), g.n) for g in graphs]
+    res = torch.full((len(graphs), 4), -7, dtype=torch.int32).pin_memory()
+    orders = torch.full((sum(g.n for g in graphs),), -7, dtype=torch.int32).pin_memory()
+    B.chordal_test_batch_host(ctx, host_rows, res, orders)
+    check(graphs, res.numpy(), orders.numpy())
+    # results only, from pageable numpy rows, twice in a row (the workspace is reused)
+    for _ in range(2):
+        res2 = np.full((len(graphs), 4), -7, dtype=np.int32)
+        B.chordal_test_batch_host(ctx, [(g.rows, g.n) for g in graphs], res2)
+        for k, g in enumerate(graphs):
+            assert tuple(res2[k].tolist()) == oracle.chordal_test(g).witness, k
+
+
+def test_batch_host_entry_full_size_pair(ctx):
+    g, h, _ = gg.large_dense_pair()
+    res = np.full((2, 4), -7, dtype=np.int32)
+    B.chordal_test_batch_host(ctx, [(g.rows, g.n), (h.rows, h.n)], res)
+    assert [tuple(r) for r in res.tolist()] == [oracle.chordal_test(g).witness, oracle.chordal_test(h).witness]

@@ -47,14 +47,17 @@ def mix():
     graphs.append(gg.close_cycles_csr(gg.peo_csr(15000, 12), 2, 12)[0])
     graphs.append(gg.empty_dense(0))
     graphs.append(gg.cycle(4))
-    return graphs, [oracle.chordal_test(g).witness for g in graphs]
+    tests = [oracle.chordal_test(g) for g in graphs]
+    return graphs, [t.witness for t in tests], [t.order for t in tests]
 
 
 def test_mixed_stream_matches_oracle_and_alone(mix):
-    graphs, want = mix
+    """Each query's verdict, witness and LexBFS order are bit-exact, in the
+    mix (batches overlapping in flight) and alone."""
+    graphs, want, want_order = mix
     dev = [to_dev(g) for g in graphs]
     with B.Context(0) as ctx:
-        q = B.Queue(ctx, mem_budget_bytes=1 << 30, max_inflight=4, max_batch=16)
+        q = B.Queue(ctx, mem_budget_bytes=1 << 30, max_inflight=4, max_batch=16, keep_orders=True)
         tickets = []
         for k, dg in enumerate(dev):       # staggered arrivals so batches overlap in flight
             tickets.append(submit(q, dg))
@@ -62,24 +65,57 @@ def test_mixed_stream_matches_oracle_and_alone(mix):
                 time.sleep(0.0005)
         assert q.drain(int(120e9)) == B.CG_OK
         mixed = []
-        for t in tickets:
-            st, res, lat = q.poll(t)
+        for t, wo in zip(tickets, want_order):
+            st, res, lat, order = q.poll(t, with_order=True)
             assert st == B.CG_OK and lat > 0
+            assert np.array_equal(order, wo)
             mixed.append(res)
         assert mixed == want
         st = q.stats()
         assert st["completed"] == len(graphs) and st["batches"] >= 3
         # each graph alone through the queue
-        for dg, w in zip(dev, want):
+        for dg, w, wo in zip(dev, want, want_order):
             t = submit(q, dg)
             assert q.drain(int(60e9)) == B.CG_OK
-            st, res, _ = q.poll(t)
-            assert st == B.CG_OK and res == w
+            st, res, _, order = q.poll(t, with_order=True)
+            assert st == B.CG_OK and res == w and np.array_equal(order, wo)
+        q.close()
+
+
+def test_orders_need_keep_orders(mix):
+    graphs, want, _ = mix
+    with B.Context(0) as ctx:
+        q = B.Queue(ctx, mem_budget_bytes=64 << 20)
+        t = submit(q, to_dev(graphs[0]))
+        assert q.drain(int(60e9)) == B.CG_OK
+        st, _, _, _ = q.poll(t, with_order=True)
+        assert st == B.CG_EINVAL                            # this queue keeps no orders
+        assert q.poll(t)[0:2] == (B.CG_OK, want[0])         # the ticket is still there
+        q.close()
+
+
+def test_csr_queries_checked_at_submit_when_validating():
+    """With cfg.validate a malformed CSR query is refused at submit (it never
+    reaches a kernel); well-formed ones are served."""
+    c = gg.dense_to_csr(gg.subtree_dense(300, 40, 3))
+    rp = torch.from_numpy(c.row_ptr).to(DEV)
+    col_ok = torch.from_numpy(c.col).to(DEV)
+    bad = c.col.copy()
+    bad[5] = c.n                                            # a column index out of range
+    col_bad = torch.from_numpy(bad).to(DEV)
+    with B.Context(0, validate=1) as ctx:
+        q = B.Queue(ctx, mem_budget_bytes=64 << 20)
+        with pytest.raises(B.ChordalError) as e:
+            q.submit_csr(rp, col_bad, c.n)
+        assert e.value.status == B.CG_EINVAL
+        t = q.submit_csr(rp, col_ok, c.n)
+        assert q.drain(int(60e9)) == B.CG_OK
+        assert q.poll(t)[0:2] == (B.CG_OK, oracle.chordal_test(c).witness)
         q.close()
 
 
 def test_memory_budget_admission_and_oversize(mix):
-    graphs, want = mix
+    graphs, want, _ = mix
     big = gg.subtree_dense(16384, 562, 3)                  # 32 MiB rows, ~0.4 MiB of scratch
     with B.Context(0) as ctx:
         q = B.Queue(ctx, mem_budget_bytes=2 << 20, max_inflight=2, max_batch=64)   # 2 MiB pool

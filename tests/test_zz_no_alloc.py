@@ -15,6 +15,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import graphgen as gg  # noqa: E402
+import oracle  # noqa: E402
 from paper_1508_06329_gb300 import binding as B  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -71,3 +72,36 @@ def test_noalloc_rejects_graphs_over_the_limit():
     st = B.cg_chordal_test_dense_noalloc(ctypes.byref(d), res.data_ptr(), None, None)
     assert st == B.CG_EINVAL
     assert b"16384" in B.cg_last_error_string()
+
+
+def test_noalloc_matches_the_oracle_including_empty_and_tiny_graphs():
+    """Also against the oracle directly (not only the context entry), for the
+    empty graph, one vertex, a ragged row length and a full-size graph."""
+    g16, h16, _ = gg.large_dense_pair()
+    for g in (gg.empty_dense(0), gg.empty_dense(1), gg.cycle(4), gg.random_dense(33, 0.3, 5), g16, h16):
+        rows = _rows(g)
+        want = oracle.chordal_test(g)
+        res, order = _noalloc(g, rows)
+        assert tuple(res) == want.witness
+        assert order == [int(x) for x in want.order]
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After a first call (which resolves the scratch array's address and may
+    load the library's device code), further calls leave the device's free
+    memory unchanged: the entry point allocates nothing."""
+    g = gg.subtree_dense(16384, 562, 5)
+    rows = _rows(g)
+    res = torch.empty(4, dtype=torch.int32, device=DEV)
+    order = torch.empty(g.n, dtype=torch.int32, device=DEV)
+    d = B.cg_dense(g.n, g.words, rows.data_ptr())
+    stream = torch.cuda.current_stream().cuda_stream
+    assert B.cg_chordal_test_dense_noalloc(ctypes.byref(d), res.data_ptr(), order.data_ptr(), stream) == B.CG_OK
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    for _ in range(4):
+        assert B.cg_chordal_test_dense_noalloc(ctypes.byref(d), res.data_ptr(), None, stream) == B.CG_OK
+        assert B.cg_chordal_test_dense_noalloc(ctypes.byref(d), res.data_ptr(), order.data_ptr(), stream) == B.CG_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+    assert tuple(res.cpu().tolist()) == oracle.chordal_test(g).witness
