@@ -366,6 +366,22 @@ int cg_autotune_set(cg_context *ctx, const int32_t *threads, int32_t slots);
 int cg_profile_read(cg_context *ctx, cg_profile *out);
 
 /*
+ * Bounds-checking build (compiled with -DCG_BOUNDS_CHECK into
+ * libchordal_debug.so; a debugging aid, not part of the paper): the state
+ * arrays of the dense and CSR searches and the check's indices are checked;
+ * an out-of-range index is recorded (array code << 56 | index) in a device
+ * error word and redirected to a scratch element instead of going out of
+ * bounds, and the launching entry point synchronises and returns CG_ECUDA
+ * with the description (cg_last_error_string).  cg_version() names the build.
+ *   cg_debug_describe  the description of an error word (any build)
+ *   cg_debug_inject    makes the next dense LexBFS launch record code (1..255)
+ *                      without any out-of-range access, to test the error
+ *                      path; CG_EINVAL in the release build
+ */
+int cg_debug_describe(uint64_t word, char *buf, int32_t len);
+int cg_debug_inject(int32_t code);
+
+/*
  * Latency floors of one step of the sequential LexBFS loop (measurement aid,
  * not part of the paper; Section 6.1 runs n dependent steps, so a step's
  * fixed costs bound the whole order).  Synchronises `stream`; allocates and

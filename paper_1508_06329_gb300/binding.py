@@ -13,7 +13,10 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libchordal.so")
+# CG_LIBCHORDAL selects another build of the library (e.g. the bounds-checking
+# libchordal_debug.so); the default is the release build next to this file.
+LIB_PATH = os.environ.get("CG_LIBCHORDAL") or os.path.join(HERE, "libchordal.so")
+DEBUG_LIB_PATH = os.path.join(HERE, "libchordal_debug.so")
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA, CG_ETIMEOUT, CG_EAGAIN = range(6)
 _STATUS = {0: "CG_OK", 1: "CG_EINVAL", 2: "CG_ENOMEM", 3: "CG_ECUDA", 4: "CG_ETIMEOUT", 5: "CG_EAGAIN"}
@@ -115,6 +118,8 @@ SIGNATURES = {
     "cg_autotune_set": ([P, P, I32], ctypes.c_int),
     "cg_profile_read": ([P, P], ctypes.c_int),
     "cg_step_floor": ([P, I32, I32, I64, I32, P, P], ctypes.c_int),
+    "cg_debug_describe": ([ctypes.c_uint64, P, I32], ctypes.c_int),
+    "cg_debug_inject": ([I32], ctypes.c_int),
 }
 
 _lock = threading.Lock()
@@ -171,6 +176,8 @@ cg_peo_check_csr = _fn("cg_peo_check_csr")
 cg_chordal_test_csr = _fn("cg_chordal_test_csr")
 cg_chordal_test_csr_host = _fn("cg_chordal_test_csr_host")
 cg_chordal_test_dense_noalloc = _fn("cg_chordal_test_dense_noalloc")
+cg_debug_describe = _fn("cg_debug_describe")
+cg_debug_inject = _fn("cg_debug_inject")
 cg_profile_enable = _fn("cg_profile_enable")
 cg_queue_create = _fn("cg_queue_create")
 cg_queue_submit = _fn("cg_queue_submit")

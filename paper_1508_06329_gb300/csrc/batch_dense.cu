@@ -133,6 +133,7 @@ int launch_fused(const FusedPlan &plan, const DenseDesc *descs, int count, int c
     CG_CUDA_TRY(cudaMemsetAsync(work_counter, 0, sizeof(int), stream));
     kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, count, order, pos, parent, res, work_counter);
     CG_LAUNCH_CHECK("chordal_dense_fused_kernel");
+    CG_DEBUG_CHECK(stream, "chordal_dense_fused_kernel");
     return CG_OK;
 }
 

@@ -24,6 +24,40 @@ int set_error(int status, const char *fmt, ...) {
     return status;
 }
 
+const char *cg_debug_array_name(unsigned code) {
+    switch (code) {
+        case kChkCls: return "dense LexBFS cls";
+        case kChkChild: return "dense LexBFS child";
+        case kChkFree: return "dense LexBFS free stack";
+        case kChkCnext: return "dense LexBFS class next";
+        case kChkCprev: return "dense LexBFS class prev";
+        case kChkSize: return "dense LexBFS class size";
+        case kChkNumbered: return "dense LexBFS numbered mask";
+        case kChkRow: return "dense LexBFS pivot row";
+        case kChkCsrCls: return "CSR LexBFS cls";
+        case kChkCsrVnext: return "CSR LexBFS vnext";
+        case kChkCsrVprev: return "CSR LexBFS vprev";
+        case kChkCsrCnext: return "CSR LexBFS class next";
+        case kChkCsrCprev: return "CSR LexBFS class prev";
+        case kChkCsrCfirst: return "CSR LexBFS class first";
+        case kChkCsrClast: return "CSR LexBFS class last";
+        case kChkCsrCsize: return "CSR LexBFS class size";
+        case kChkCsrCmoved: return "CSR LexBFS class moved";
+        case kChkCsrCchild: return "CSR LexBFS class child";
+        case kChkCsrFree: return "CSR LexBFS free stack";
+        case kChkCsrSy: return "CSR LexBFS long-row vertices";
+        case kChkCsrSop: return "CSR LexBFS long-row old prev";
+        case kChkCsrSon: return "CSR LexBFS long-row old next";
+        case kChkCsrSrun: return "CSR LexBFS long-row runs";
+        case kChkCsrSkey: return "CSR LexBFS long-row keys";
+        case kChkUnitMask: return "check earlier-than mask";
+        case kChkUnitPos: return "check pos gather";
+        case kChkUnitGroup: return "check order / parent value";
+        case kChkInjected: return "injected test entry";
+        default: return "unknown array";
+    }
+}
+
 }  // namespace cg
 
 using namespace cg;
@@ -460,7 +494,27 @@ int run_single_csr(cg_context *ctx, const cg_csr *g, int32_t *order_out, int32_t
 
 extern "C" {
 
-const char *cg_version(void) { return "chordal-gb300 0.1.0 (sm_103a)"; }
+#ifdef CG_BOUNDS_CHECK
+const char *cg_version(void) { return "chordal-gb300 0.2.0 (sm_103a, bounds-checking build)"; }
+#else
+const char *cg_version(void) { return "chordal-gb300 0.2.0 (sm_103a)"; }
+#endif
+
+int cg_debug_describe(uint64_t word, char *buf, int32_t len) {
+    if (!buf || len <= 0) return set_error(CG_EINVAL, "null or empty message buffer");
+    if (!word) {
+        snprintf(buf, (size_t)len, "no bounds-check error");
+        return CG_OK;
+    }
+    snprintf(buf, (size_t)len, "%s index %llu out of range", cg_debug_array_name((unsigned)(word >> 56)),
+             (unsigned long long)(word & ((1ull << 56) - 1)));
+    return CG_OK;
+}
+
+int cg_debug_inject(int32_t code) {
+    if (code <= 0 || code > 255) return set_error(CG_EINVAL, "code must be in 1..255");
+    return debug_inject((unsigned)code);
+}
 
 const char *cg_last_error_string(void) { return cg::g_err; }
 

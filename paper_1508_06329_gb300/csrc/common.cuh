@@ -20,6 +20,34 @@ int set_error(int status, const char *fmt, ...);
                                    cudaGetErrorString(e_), __FILE__, __LINE__);            \
     } while (0)
 
+// Describes a bounds-check error word (host side; the release build never sets one).
+const char *cg_debug_array_name(unsigned code);
+
+#ifdef CG_BOUNDS_CHECK
+// After a launch: synchronise, read and clear this translation unit's error word.
+// (Skipped while the stream is being captured into a CUDA graph: a batch plan
+// replays unchecked launches.)
+#define CG_DEBUG_CHECK(stream, what)                                                        \
+    do {                                                                                    \
+        cudaStreamCaptureStatus cs_ = cudaStreamCaptureStatusNone;                          \
+        if (cudaStreamIsCapturing(stream, &cs_) != cudaSuccess || cs_ != cudaStreamCaptureStatusNone) break; \
+        cudaError_t e_ = cudaStreamSynchronize(stream);                                     \
+        unsigned long long w_ = 0, z_ = 0;                                                  \
+        if (e_ == cudaSuccess) e_ = cudaMemcpyFromSymbol(&w_, ::cg::cg_dbg_word, sizeof(w_)); \
+        if (e_ == cudaSuccess && w_) e_ = cudaMemcpyToSymbol(::cg::cg_dbg_word, &z_, sizeof(z_)); \
+        if (e_ != cudaSuccess)                                                              \
+            return ::cg::set_error(CG_ECUDA, "%s: %s", what, cudaGetErrorString(e_));      \
+        if (w_)                                                                             \
+            return ::cg::set_error(CG_ECUDA, "bounds check in %s: %s index %llu out of range", what, \
+                                   ::cg::cg_debug_array_name((unsigned)(w_ >> 56)),        \
+                                   (unsigned long long)(w_ & ((1ull << 56) - 1)));          \
+    } while (0)
+#else
+#define CG_DEBUG_CHECK(stream, what) \
+    do {                             \
+    } while (0)
+#endif
+
 #define CG_LAUNCH_CHECK(what)                                                              \
     do {                                                                                   \
         cudaError_t e_ = cudaGetLastError();                                               \
@@ -48,6 +76,59 @@ __device__ __forceinline__ void prefetch_range_l2(const void *base, size_t bytes
         prefetch_l2_bulk(reinterpret_cast<const void *>(a16 + off), len);
     }
 }
+
+// ---- bounds-checking build (-DCG_BOUNDS_CHECK)
+// The state arrays of the searches and the check are declared CG_ARR(T): a
+// plain pointer in the release build; in the bounds-checking build a pointer
+// with its length, whose operator[] records an out-of-range index in the
+// translation unit's error word (array code and index; the first one wins)
+// and redirects the access to a scratch element instead of going out of
+// bounds.  Each launcher then synchronises and turns a non-zero word into
+// CG_ECUDA with a description (CG_DEBUG_CHECK).
+#ifdef CG_BOUNDS_CHECK
+static __device__ unsigned long long cg_dbg_word;       // this translation unit's error word
+static __device__ unsigned long long cg_dbg_sink[2];    // target of redirected accesses
+
+__device__ __forceinline__ void cg_dbg_record(unsigned code, unsigned long long idx) {
+    atomicCAS(&cg_dbg_word, 0ull, ((unsigned long long)(code & 0xFFu) << 56) | (idx & ((1ull << 56) - 1)));
+}
+
+template <typename T>
+struct Chk {
+    T *p;
+    unsigned long long n;
+    unsigned code;
+    __device__ T &operator[](long long i) const {
+        if ((unsigned long long)i >= n) {
+            cg_dbg_record(code, (unsigned long long)i);
+            return *reinterpret_cast<T *>(cg_dbg_sink);
+        }
+        return p[i];
+    }
+    __host__ __device__ operator T *() const { return p; }
+};
+template <typename T>
+__device__ __forceinline__ Chk<T> cg_arr(T *p, unsigned long long n, unsigned code) {
+    return Chk<T>{p, n, code};
+}
+#define CG_ARR(T) ::cg::Chk<T>
+#else
+template <typename T>
+__device__ __forceinline__ T *cg_arr(T *p, unsigned long long, unsigned) {
+    return p;
+}
+#define CG_ARR(T) T *
+#endif
+
+// Array codes of the bounds-checking build (the high byte of the error word).
+enum : unsigned {
+    kChkCls = 1, kChkChild, kChkFree, kChkCnext, kChkCprev, kChkSize, kChkNumbered, kChkRow,
+    kChkCsrCls = 16, kChkCsrVnext, kChkCsrVprev, kChkCsrCnext, kChkCsrCprev, kChkCsrCfirst, kChkCsrClast,
+    kChkCsrCsize, kChkCsrCmoved, kChkCsrCchild, kChkCsrFree, kChkCsrSy, kChkCsrSop, kChkCsrSon, kChkCsrSrun,
+    kChkCsrSkey,
+    kChkUnitMask = 40, kChkUnitPos, kChkUnitRow, kChkUnitGroup,
+    kChkInjected = 255,
+};
 
 // Parent value meaning "not known yet": the dense check finds it.
 constexpr int kParentUnresolved = -2;

@@ -35,6 +35,10 @@ int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc s
                         int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
                         cudaStream_t stream, int parent_mode = 0, unsigned long long *keys = nullptr);
 
+// Bounds-checking build: the next dense LexBFS launch records `code` (a test
+// of the error path); CG_EINVAL in the release build.
+int debug_inject(unsigned code);
+
 // ---- dense perfect-elimination check (peo_dense.cu)
 // keys: device u64[count], set to ~0 by the launcher.
 // parent_known: parent[] already holds p(v) (from the search); otherwise the

@@ -43,13 +43,22 @@ constexpr int kNumberedCls = -2;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct CsrState {
-    int *cls, *vnext, *vprev;               // [n]
-    int *cnext, *cprev;                     // [n + 1], index n = head sentinel
-    int *cfirst, *clast, *csize;            // [n]
-    int *cmoved, *cchild;                   // [n]  long-row step: moved count, new id (0 / kNone between steps)
-    int *freel;                             // [n]
-    int *sy, *sop, *son, *srun;             // [max_deg] long-row scratch by row position / sorted index
-    unsigned long long *skey;               // [next pow2 >= max_deg] (class << 32 | row position) keys
+    CG_ARR(int) cls;                        // [n] class of each vertex
+    CG_ARR(int) vnext;                      // [n] member lists
+    CG_ARR(int) vprev;                      // [n]
+    CG_ARR(int) cnext;                      // [n + 1] class list, index n = head sentinel
+    CG_ARR(int) cprev;                      // [n + 1]
+    CG_ARR(int) cfirst;                     // [n] per class: first, last member, size
+    CG_ARR(int) clast;                      // [n]
+    CG_ARR(int) csize;                      // [n]
+    CG_ARR(int) cmoved;                     // [n] long-row step: moved count (0 between steps)
+    CG_ARR(int) cchild;                     // [n] long-row step: new id (kNone between steps)
+    CG_ARR(int) freel;                      // [n] free class ids
+    CG_ARR(int) sy;                         // [max_deg] long-row scratch by row position / sorted index
+    CG_ARR(int) sop;                        // [max_deg]
+    CG_ARR(int) son;                        // [max_deg]
+    CG_ARR(int) srun;                       // [max_deg]
+    CG_ARR(unsigned long long) skey;        // [next pow2 >= max_deg] (class << 32 | row position) keys
 };
 
 constexpr int kCsrArrays = 11;
@@ -66,18 +75,26 @@ __device__ inline CsrState csr_state_carve(int *base, int64_t n, int64_t max_deg
     CsrState s;
     int *p = base;
     const int64_t stride = ((n + 1 + 31) / 32) * 32;
-    int **arrs[kCsrArrays] = {&s.cls,   &s.vnext,  &s.vprev,  &s.cnext,  &s.cprev, &s.cfirst,
-                              &s.clast, &s.csize,  &s.cmoved, &s.cchild, &s.freel};
-    for (int a = 0; a < kCsrArrays; ++a) {
-        *arrs[a] = p;
-        p += stride;
-    }
+    // kCsrArrays blocks of stride ints, in this order
+    s.cls = cg_arr(p, n, kChkCsrCls); p += stride;
+    s.vnext = cg_arr(p, n, kChkCsrVnext); p += stride;
+    s.vprev = cg_arr(p, n, kChkCsrVprev); p += stride;
+    s.cnext = cg_arr(p, n + 1, kChkCsrCnext); p += stride;
+    s.cprev = cg_arr(p, n + 1, kChkCsrCprev); p += stride;
+    s.cfirst = cg_arr(p, n, kChkCsrCfirst); p += stride;
+    s.clast = cg_arr(p, n, kChkCsrClast); p += stride;
+    s.csize = cg_arr(p, n, kChkCsrCsize); p += stride;
+    s.cmoved = cg_arr(p, n, kChkCsrCmoved); p += stride;
+    s.cchild = cg_arr(p, n, kChkCsrCchild); p += stride;
+    s.freel = cg_arr(p, n, kChkCsrFree); p += stride;
     const int64_t ds = (((max_deg > 1 ? max_deg : 1) + 31) / 32) * 32;
-    s.sy = p; p += ds;
-    s.sop = p; p += ds;
-    s.son = p; p += ds;
-    s.srun = p; p += ds;
-    s.skey = reinterpret_cast<unsigned long long *>(p);   // p stays 8-byte aligned: every block is 32 ints
+    const int64_t md = max_deg > 1 ? max_deg : 1;
+    s.sy = cg_arr(p, md, kChkCsrSy); p += ds;
+    s.sop = cg_arr(p, md, kChkCsrSop); p += ds;
+    s.son = cg_arr(p, md, kChkCsrSon); p += ds;
+    s.srun = cg_arr(p, md, kChkCsrSrun); p += ds;
+    // p stays 8-byte aligned: every block is 32 ints
+    s.skey = cg_arr(reinterpret_cast<unsigned long long *>(p), pow2_at_least(md), kChkCsrSkey);
     return s;
 }
 
@@ -587,6 +604,7 @@ int lexbfs_csr_launch(int n, int64_t max_deg, const int64_t *row_ptr, const int3
     lexbfs_csr_kernel<<<1, kCsrThreads, 0, stream>>>(static_cast<int *>(ws), n, max_deg, row_ptr, col, nnz, order,
                                                      pos, parent);
     CG_LAUNCH_CHECK("lexbfs_csr_kernel");
+    CG_DEBUG_CHECK(stream, "lexbfs_csr_kernel");
     return CG_OK;
 }
 

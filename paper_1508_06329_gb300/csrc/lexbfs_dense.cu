@@ -6,6 +6,13 @@
 
 namespace cg {
 
+#ifdef CG_BOUNDS_CHECK
+// A code set by cg_debug_inject: the next dense LexBFS launch records it as a
+// bounds-check error without touching memory out of range (a test of the
+// status path).
+static __device__ unsigned cg_dbg_inject_code;
+#endif
+
 namespace {
 
 constexpr size_t kSmemLimit = 227 * 1024;   // opt-in dynamic shared memory per CTA (sm_100 family)
@@ -22,6 +29,12 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
     extern __shared__ __align__(16) unsigned char smem[];
     LexScalars *sc = reinterpret_cast<LexScalars *>(smem);
     unsigned char *free_smem = smem + kLexScalarBytes;
+#ifdef CG_BOUNDS_CHECK
+    if (blockIdx.x == 0 && threadIdx.x == 0 && cg_dbg_inject_code) {
+        cg_dbg_record(cg_dbg_inject_code, 0ull);
+        cg_dbg_inject_code = 0u;
+    }
+#endif
     for (;;) {
         if (threadIdx.x == 0) sc->next_graph = count == 1 ? (int)blockIdx.x : atomicAdd(work_counter, 1);
         __syncthreads();
@@ -81,6 +94,7 @@ int launch_variant(const LexPlan &plan, const DenseDesc *descs, DenseDesc single
         CG_CUDA_TRY(cudaMemsetAsync(keys + count, 0, 2 * sizeof(unsigned long long), stream));
     }
     CG_LAUNCH_CHECK("lexbfs_dense_kernel");
+    CG_DEBUG_CHECK(stream, "lexbfs_dense_kernel");
     return CG_OK;
 }
 
@@ -152,6 +166,16 @@ int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc s
         default:
             return go(launch_variant<uint16_t, 1024, 1, 2, false>, nullptr);
     }
+}
+
+int debug_inject(unsigned code) {
+#ifdef CG_BOUNDS_CHECK
+    CG_CUDA_TRY(cudaMemcpyToSymbol(cg_dbg_inject_code, &code, sizeof(code)));
+    return CG_OK;
+#else
+    (void)code;
+    return set_error(CG_EINVAL, "not a bounds-checking build (CG_BOUNDS_CHECK)");
+#endif
 }
 
 }  // namespace cg

@@ -64,13 +64,13 @@ struct IdTraits<uint32_t> {
 
 template <typename Id>
 struct LexState {
-    typename IdTraits<Id>::Sz *sz;  // [n]     size | moved-this-step << kShift
-    Id *cls;                        // [n]     class of each vertex, kNumbered once visited
-    Id *child;                      // [n]     class receiving a class's pivot neighbours
-    Id *freel;                      // [n]     stack of unused class ids
-    Id *cnext;                      // [n + 1] class list; index n is the head sentinel
-    Id *cprev;                      // [n + 1]
-    uint32_t *numbered;             // [ceil(n/32)] bit v set once v is visited
+    CG_ARR(typename IdTraits<Id>::Sz) sz;  // [n]     size | moved-this-step << kShift
+    CG_ARR(Id) cls;                        // [n]     class of each vertex, kNumbered once visited
+    CG_ARR(Id) child;                      // [n]     class receiving a class's pivot neighbours
+    CG_ARR(Id) freel;                      // [n]     stack of unused class ids
+    CG_ARR(Id) cnext;                      // [n + 1] class list; index n is the head sentinel
+    CG_ARR(Id) cprev;                      // [n + 1]
+    CG_ARR(uint32_t) numbered;             // [ceil(n/32)] bit v set once v is visited
 };
 
 struct LexScalars {
@@ -98,15 +98,15 @@ template <typename Id>
 __device__ inline LexState<Id> lex_state_carve(unsigned char *base, int n) {
     using Sz = typename IdTraits<Id>::Sz;
     LexState<Id> s;
-    s.sz = reinterpret_cast<Sz *>(base);
+    s.sz = cg_arr(reinterpret_cast<Sz *>(base), n, kChkSize);
     Id *p = reinterpret_cast<Id *>(base + (size_t)n * sizeof(Sz));
-    s.cls = p;
-    s.child = p + n;
-    s.freel = p + 2 * (size_t)n;
-    s.cnext = p + 3 * (size_t)n;
-    s.cprev = p + 4 * (size_t)n + 1;
+    s.cls = cg_arr(p, n, kChkCls);
+    s.child = cg_arr(p + n, n, kChkChild);
+    s.freel = cg_arr(p + 2 * (size_t)n, n, kChkFree);
+    s.cnext = cg_arr(p + 3 * (size_t)n, n + 1, kChkCnext);
+    s.cprev = cg_arr(p + 4 * (size_t)n + 1, n + 1, kChkCprev);
     size_t b = (size_t)n * sizeof(Sz) + (size_t)n * sizeof(Id) * 3 + (size_t)(n + 1) * sizeof(Id) * 2;
-    s.numbered = reinterpret_cast<uint32_t *>(base + ((b + 15) & ~size_t(15)));
+    s.numbered = cg_arr(reinterpret_cast<uint32_t *>(base + ((b + 15) & ~size_t(15))), (n + 31) / 32, kChkNumbered);
     return s;
 }
 
@@ -134,20 +134,27 @@ template <typename Id>
 __device__ inline LexState<Id> lex_state_carve_split(unsigned char *smem, unsigned char *gmem, int n) {
     using Sz = typename IdTraits<Id>::Sz;
     LexState<Id> s;
-    s.cls = reinterpret_cast<Id *>(smem);
-    s.numbered = reinterpret_cast<uint32_t *>(smem + (((size_t)n * sizeof(Id) + 15) & ~size_t(15)));
-    s.sz = reinterpret_cast<Sz *>(gmem);
+    s.cls = cg_arr(reinterpret_cast<Id *>(smem), n, kChkCls);
+    s.numbered = cg_arr(reinterpret_cast<uint32_t *>(smem + (((size_t)n * sizeof(Id) + 15) & ~size_t(15))),
+                        (n + 31) / 32, kChkNumbered);
+    s.sz = cg_arr(reinterpret_cast<Sz *>(gmem), n, kChkSize);
     Id *p = reinterpret_cast<Id *>(gmem + (size_t)n * sizeof(Sz));
-    s.child = p;
-    s.freel = p + n;
-    s.cnext = p + 2 * (size_t)n;
-    s.cprev = p + 3 * (size_t)n + 1;
+    s.child = cg_arr(p, n, kChkChild);
+    s.freel = cg_arr(p + n, n, kChkFree);
+    s.cnext = cg_arr(p + 2 * (size_t)n, n + 1, kChkCnext);
+    s.cprev = cg_arr(p + 3 * (size_t)n + 1, n + 1, kChkCprev);
     return s;
 }
 
 // Word w of row x, padding bits cleared.
 __device__ __forceinline__ uint32_t row_word(const uint32_t *__restrict__ rows, int stride, int x, int w,
                                              int wn, uint32_t lastmask) {
+#ifdef CG_BOUNDS_CHECK
+    if ((unsigned)w >= (unsigned)wn || x < 0) {   // x < n holds when x comes from the state arrays
+        cg_dbg_record(kChkRow, (unsigned long long)(unsigned)x);
+        return 0u;
+    }
+#endif
     uint32_t v = rows[(size_t)x * stride + w];
     return w == wn - 1 ? (v & lastmask) : v;
 }

@@ -455,6 +455,9 @@ __global__ void __launch_bounds__(kUnitThreads) peo_unit_kernel(const DenseDesc 
                 g0 + lane < n && ((unsigned)v >= (unsigned)n || p >= n || (p < -1 && p != kParentUnresolved));
             if (bad) {
                 atomicOr(keys + count + 1, 2ull);
+#ifdef CG_BOUNDS_CHECK
+                cg_dbg_record(kChkUnitGroup, (unsigned long long)(g0 + lane));
+#endif
                 v = 0;
                 p = -1;
             }
@@ -503,6 +506,12 @@ __global__ void __launch_bounds__(kUnitThreads) peo_unit_kernel(const DenseDesc 
                 for (int k = 0; k < kGatherWords; ++k) {
                     const int w = w0 + lane + 32 * k;
                     int pu[32];
+#ifdef CG_BOUNDS_CHECK
+                    if (rw[k] && (w << 5) + 31 - __clz(rw[k]) >= n) {
+                        cg_dbg_record(kChkUnitPos, (unsigned long long)((w << 5) + 31 - __clz(rw[k])));
+                        rw[k] = 0u;
+                    }
+#endif
 #pragma unroll
                     for (int b = 0; b < 32; ++b) pu[b] = (rw[k] >> b) & 1u ? __ldg(pos_g + (w << 5) + b) : -1;
 #pragma unroll
@@ -550,6 +559,9 @@ __global__ void __launch_bounds__(kUnitThreads) peo_unit_kernel(const DenseDesc 
 #pragma unroll
                 for (int it = 0; it < kPosChunk; ++it) {   // a lane's words rise with (it, k): its first hit is its lowest
                     const int w4 = c + 128 * it + 4 * lane;
+#ifdef CG_BOUNDS_CHECK
+                    if (w4 < wn && w4 + 3 >= mask_stride(n)) cg_dbg_record(kChkUnitMask, (unsigned long long)w4);
+#endif
                     const uint4 e = w4 < wn ? *reinterpret_cast<const uint4 *>(sE + w4) : make_uint4(0u, 0u, 0u, 0u);
                     const uint32_t aa[4] = {a[it].x, a[it].y, a[it].z, a[it].w};
                     const uint32_t bb[4] = {b[it].x, b[it].y, b[it].z, b[it].w};
@@ -678,6 +690,7 @@ int peo_unit_launch(const DenseDesc *descs, DenseDesc single, int count, int n_m
                                                                      res);
     }
     CG_LAUNCH_CHECK("peo_unit_kernel");
+    CG_DEBUG_CHECK(stream, "peo_unit_kernel");
     return CG_OK;
 }
 
