@@ -199,7 +199,11 @@ int cg_peo_check_csr(cg_context *ctx, const cg_csr *g, const int32_t *order, int
                      cudaStream_t stream);
 
 /* The whole test on one CSR graph.  res device cg_result; order device
- * int32[n] or NULL. */
+ * int32[n] or NULL.  CSR graphs with n <= 131072 and at least 64 neighbours
+ * per vertex on average (or n <= 4096) are expanded to bit rows in the
+ * workspace (n * ceil(n/32) * 4 bytes more) and take the dense kernels, which
+ * are faster there; the order and witness are the same (cg_lexbfs_order_csr
+ * and cg_chordal_test_csr_host route the same way). */
 int cg_chordal_test_csr(cg_context *ctx, const cg_csr *g, cg_result *res, int32_t *order, cudaStream_t stream);
 
 /* The CSR test with HOST buffers (row_ptr int64[n+1], col int32[nnz]); copies
@@ -274,7 +278,7 @@ int cg_chordal_test_dense_noalloc(const cg_dense *g, cg_result *res, int32_t *or
  * batch on its slot's stream (so queries that arrive while others run
  * overlap with them on the GPU), and marks tickets done when the batch's
  * event completes.  Dense queries and CSR queries with n <= 131072 and at
- * least 16 neighbours per vertex on average (or n <= 4096) use the dense
+ * least 64 neighbours per vertex on average (or n <= 4096) use the dense
  * kernels (CSR rows are expanded to bits on the device); sparser CSR queries
  * use the CSR kernels.  Results equal those of the single-graph entries.
  * The graph memory of a query must stay valid until its ticket completes.

@@ -133,7 +133,7 @@ int peo_csr_launch(int n, const int64_t *row_ptr, const int32_t *col, const int3
 int csr_to_bits_launch(int n, const int64_t *row_ptr, const int32_t *col, uint32_t *rows, int words, int num_sms,
                        cudaStream_t stream);
 // CSR graphs dense enough for the dense kernels: n <= kCsrDenseMaxN and at
-// least 16 neighbours per vertex on average (or n <= 4096); the single-graph
+// least 64 neighbours per vertex on average (or n <= 4096); the single-graph
 // CSR entries and the serving queue expand these to bit rows first.
 constexpr int kCsrDenseMaxN = 131072;
 bool csr_takes_dense_path(int n, int64_t nnz);

@@ -42,6 +42,8 @@ constexpr int kNone = -1;
 constexpr int kNumberedCls = -2;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+#ifdef CG_BOUNDS_CHECK
+// the bounds-checking build: every state array carries its length
 struct CsrState {
     CG_ARR(int) cls;                        // [n] class of each vertex
     CG_ARR(int) vnext;                      // [n] member lists
@@ -97,6 +99,48 @@ __device__ inline CsrState csr_state_carve(int *base, int64_t n, int64_t max_deg
     s.skey = cg_arr(reinterpret_cast<unsigned long long *>(p), pow2_at_least(md), kChkCsrSkey);
     return s;
 }
+
+#else
+struct CsrState {
+    int *cls, *vnext, *vprev;               // [n]
+    int *cnext, *cprev;                     // [n + 1], index n = head sentinel
+    int *cfirst, *clast, *csize;            // [n]
+    int *cmoved, *cchild;                   // [n]  long-row step: moved count, new id (0 / kNone between steps)
+    int *freel;                             // [n]
+    int *sy, *sop, *son, *srun;             // [max_deg] long-row scratch by row position / sorted index
+    unsigned long long *skey;               // [next pow2 >= max_deg] (class << 32 | row position) keys
+};
+
+constexpr int kCsrArrays = 11;
+constexpr int kCsrThreads = 1024;      // the CTA of the search: warp 0 walks the steps
+constexpr int kSortSmem = 4096;        // keys sorted in shared memory up to this many
+
+__host__ __device__ inline int64_t pow2_at_least(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+__device__ inline CsrState csr_state_carve(int *base, int64_t n, int64_t max_deg) {
+    CsrState s;
+    int *p = base;
+    const int64_t stride = ((n + 1 + 31) / 32) * 32;
+    int **arrs[kCsrArrays] = {&s.cls,   &s.vnext,  &s.vprev,  &s.cnext,  &s.cprev, &s.cfirst,
+                              &s.clast, &s.csize,  &s.cmoved, &s.cchild, &s.freel};
+    for (int a = 0; a < kCsrArrays; ++a) {
+        *arrs[a] = p;
+        p += stride;
+    }
+    const int64_t ds = (((max_deg > 1 ? max_deg : 1) + 31) / 32) * 32;
+    s.sy = p; p += ds;
+    s.sop = p; p += ds;
+    s.son = p; p += ds;
+    s.srun = p; p += ds;
+    s.skey = reinterpret_cast<unsigned long long *>(p);   // p stays 8-byte aligned: every block is 32 ints
+    return s;
+}
+
+#endif
 
 __host__ inline size_t csr_state_stride_bytes(int64_t n, int64_t max_deg) {
     const int64_t stride = ((n + 1 + 31) / 32) * 32;

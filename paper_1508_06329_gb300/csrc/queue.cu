@@ -15,7 +15,7 @@
 // with n <= 4096 are batched up to max_batch per launch, larger graphs up to
 // max_batch_large, each lane in arrival order; results of a batch complete
 // together.  Dense queries run the one-CTA or LexBFS-CTA + check kernels of
-// the batched path.  CSR queries with n <= 131072 and at least 16 neighbours per vertex on
+// the batched path.  CSR queries with n <= 131072 and at least 64 neighbours per vertex on
 // average (or n <= 4096) are expanded to bit rows on the device first and take
 // the same path; sparser CSR queries run the CSR kernels.
 #include <chrono>
