@@ -193,10 +193,46 @@ def make_workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the current kernel (profiles/lexbfs_dense_n16384_pair.txt):
-# lexbfs_dense_kernel on the N=16,384 pair, 68.39 MB read + 1.51 MB written.
-NCU_TRAFFIC_BYTES = {"dense16k": 68.39e6 + 1.51e6}
+# DRAM bytes (read + write) per launch of the dominant kernel come from the
+# kept ncu summary of that kernel (the "dram_bytes_per_launch" line), which
+# also records the SHA-256 of the kernel's sources at capture time
+# ("source_sha256"); once the sources differ, the figure belongs to another
+# kernel and the roofline's traffic is null.
+TRAFFIC_SUMMARIES = {
+    "dense16k": ("profiles/lexbfs_dense_n16384_pair.txt",
+                 ["paper_1508_06329_gb300/csrc/lexbfs_dense.cuh", "paper_1508_06329_gb300/csrc/lexbfs_dense.cu",
+                  "paper_1508_06329_gb300/csrc/common.cuh"]),
+}
+
+
+def sources_sha256(paths, root: str = ROOT) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(root, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(key: str, root: str = ROOT):
+    """(bytes per launch or None, note) from the kept summary of `key`'s kernel."""
+    if key not in TRAFFIC_SUMMARIES:
+        return None, "no ncu summary for this workload"
+    summary, srcs = TRAFFIC_SUMMARIES[key]
+    fields = {}
+    try:
+        with open(os.path.join(root, summary)) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+    except OSError:
+        return None, f"{summary} missing"
+    if "dram_bytes_per_launch" not in fields or "source_sha256" not in fields:
+        return None, f"{summary} has no dram_bytes_per_launch / source_sha256 line"
+    if fields["source_sha256"] != sources_sha256(srcs, root):
+        return None, f"kernel sources changed since the capture in {summary}"
+    return float(fields["dram_bytes_per_launch"]), f"ncu capture in {summary}"
 
 
 def algorithmic_bytes(g) -> int:
@@ -933,8 +969,9 @@ def run_gpu(args):
         lex_gbs = lex_bytes / (lex_ms * 1e-3) / 1e9
         chk_gbs = chk_bytes / (chk_ms * 1e-3) / 1e9
         dom_share = prof["lexbfs_ms"] / max(1e-9, prof["lexbfs_ms"] + prof["check_ms"])
+        traffic, traffic_note = ncu_traffic(wl + ("/mcs" if mcs else ""))
         roof = {"bound": "hbm", "kernel": f"{kernel} ({100 * dom_share:.1f}% of GPU time)", "achieved": lex_gbs,
-                "peak": hbm, "unit": "GB/s", "frac": lex_gbs / hbm, "traffic": NCU_TRAFFIC_BYTES.get(wl + ("/mcs" if mcs else "")),
+                "peak": hbm, "unit": "GB/s", "frac": lex_gbs / hbm, "traffic": traffic, "traffic_source": traffic_note,
                 "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": lex_bytes * per_launch}
         phases.update({"lexbfs_ms_per_launch": lex_ms, "check_ms_per_launch": chk_ms,
                        "lexbfs_ns_per_step": lex_ms * 1e6 / graphs[0].n, "check_gbs": chk_gbs,

@@ -198,6 +198,7 @@ int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const in
                 BatchLayout *L) {
     int rc;
     L->count = count;
+    L->emask_words = 0;
     std::vector<int> idx(count);
     std::vector<int> bucket(count);
     for (int k = 0; k < count; ++k) {
@@ -246,6 +247,13 @@ int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const in
             if ((rc = lexbfs_dense_plan(B.nmax, ctx->cfg.threads_override, &B.lplan))) return rc;
             B.bulk = true;
             for (int q = B.begin; q < B.end; ++q) B.bulk = B.bulk && peo_rows_vec_ok(L->descs[q]);
+            // graphs sorted largest first: nmax bounds the bucket
+            B.stage = B.bulk && B.nmax <= kStageMaxN;
+            if (B.stage)
+                for (int q = B.begin; q < B.end; ++q) {
+                    L->descs[q].ebase = L->emask_words;
+                    L->emask_words += earlier_mask_words(L->descs[q].n);
+                }
             const int by_smem =
                 B.lplan.smem_bytes ? (int)std::max<size_t>(1, (228 * 1024) / (B.lplan.smem_bytes + 1024)) : 32;
             const int by_threads = std::max(1, 2048 / B.lplan.threads);
@@ -269,6 +277,7 @@ BatchBuffers batch_buffers(const BatchLayout &L, bool need_order) {
     bb.o_counter = cv.take<int>(kBuckets * 64);
     const auto &B9 = L.bk[9];
     bb.o_gstate = cv.take<unsigned char>(B9.end > B9.begin ? B9.lplan.gstate_bytes * B9.ctas : 0);
+    bb.o_emask = cv.take<uint32_t>(L.emask_words);
     bb.bytes = cv.off;
     return bb;
 }
@@ -303,18 +312,24 @@ int enqueue_batch(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
             if (account) ctx->launches += 1;
         } else {
             int32_t *ppos = reinterpret_cast<int32_t *>(P(bb.o_ppos));
+            uint32_t *emask = B.stage ? reinterpret_cast<uint32_t *>(P(bb.o_emask)) : nullptr;
             {
                 PhaseTimer pt(tctx, &ctx->ev_lex, s);
                 if ((rc = lexbfs_dense_launch(B.lplan, ddesc + B.begin, DenseDesc{}, cnt, B.ctas, order, pos, ppos,
                                               B.lplan.gstate_bytes ? P(bb.o_gstate) : nullptr, counters + 64 * b, s,
-                                              kParentPivots, keys + B.begin)))
+                                              kParentPivots, keys + B.begin, emask, parent)))
                     return rc;
             }
             PhaseTimer pt(tctx, &ctx->ev_check, s);
-            // the position-ordered check of this bucket's graphs (masks, open parents, check)
-            if ((rc = peo_unit_launch(ddesc + B.begin, DenseDesc{}, cnt, B.nmax, B.bulk, order, pos, ppos,
-                                      keys + B.begin, res, s)))
-                return rc;
+            // the position-ordered check of this bucket's graphs: rows staged in
+            // shared memory with the search's masks, or E_b built from pos
+            if (B.stage)
+                rc = peo_stage_launch(ddesc + B.begin, DenseDesc{}, cnt, B.nmax, order, ppos, emask,
+                                      keys + B.begin, res, ctx->num_sms, s);
+            else
+                rc = peo_unit_launch(ddesc + B.begin, DenseDesc{}, cnt, B.nmax, B.bulk, order, pos, ppos,
+                                     keys + B.begin, res, s);
+            if (rc) return rc;
             if (account) ctx->launches += 2;
         }
         CG_CUDA_TRY(cudaEventRecord(ss.join[b], s));
@@ -351,7 +366,7 @@ int upload_layout(cg_context *ctx, const BatchLayout &L, const BatchBuffers &bb,
 
 // Workspace layout of run_single_dense (also the start of the host entry's).
 struct SingleDenseCarve {
-    size_t o_order, o_pos, o_parent, o_ppos, o_key, o_counter, o_gstate;
+    size_t o_order, o_pos, o_parent, o_ppos, o_key, o_counter, o_gstate, o_emask;
     Carve cv;
     SingleDenseCarve(int n, const LexPlan &plan) {
         o_order = cv.take<int32_t>(n);
@@ -361,6 +376,8 @@ struct SingleDenseCarve {
         o_key = cv.take<unsigned long long>(3);   // key, the check's CTA counter, error word
         o_counter = cv.take<int>(1);
         o_gstate = cv.take<unsigned char>(plan.gstate_bytes);
+        // the earlier-than masks of the staged check (written by the search)
+        o_emask = cv.take<uint32_t>(n > 0 && n <= kStageMaxN ? earlier_mask_words(n) : 0);
     }
 };
 
@@ -390,17 +407,20 @@ int run_single_dense(cg_context *ctx, const cg_dense *g, int32_t *order_out, int
     // with a result wanted, the search also records the parents of its pivots
     // by position (one store per step) and initialises the check's keys
     int32_t *ppos = at<int32_t>(ctx, base + sc.o_ppos);
+    const bool stage = res && peo_stage_ok(d);
+    uint32_t *emask = stage ? at<uint32_t>(ctx, base + sc.o_emask) : nullptr;
     {
         PhaseTimer pt(ctx, &ctx->ev_lex, stream);
         rc = lexbfs_dense_launch(plan, nullptr, d, 1, 1, order, pos, res ? ppos : nullptr,
                                  plan.gstate_bytes ? at<void>(ctx, base + sc.o_gstate) : nullptr, at<int>(ctx, base + sc.o_counter),
-                                 stream, kParentPivots, res ? key : nullptr);
+                                 stream, kParentPivots, res ? key : nullptr, emask, res ? parent : nullptr);
         if (rc) return rc;
         ctx->launches += 1;
     }
     if (!res) return CG_OK;
     PhaseTimer pt(ctx, &ctx->ev_check, stream);
     ctx->launches += 1;
+    if (stage) return peo_stage_launch(nullptr, d, 1, n, order, ppos, emask, key, res, ctx->num_sms, stream);
     return peo_unit_launch(nullptr, d, 1, n, peo_rows_vec_ok(d), order, pos, ppos, key, res, stream);
 }
 

@@ -88,6 +88,7 @@ struct BatchLayout {
         LexPlan lplan{};
         int ctas = 0;
         bool bulk = false;              // bucket 9: every graph's rows suit 128-bit loads
+        bool stage = false;             // bucket 9: the staged check (masks written by the search)
         int64_t vbegin = 0, vend = 0;   // packed vertex range
     };
     int count = 0;
@@ -95,11 +96,12 @@ struct BatchLayout {
     std::vector<int64_t> voff;         // packed vertex offset of each desc (+ total)
     Bucket bk[kBuckets];
     int64_t total = 0;
+    int64_t emask_words = 0;           // earlier-than masks of the staged bucket's graphs (at each ebase)
 };
 
 // Device buffers a batch needs (offsets into one allocation).
 struct BatchBuffers {
-    size_t o_desc, o_voff, o_order, o_pos, o_parent, o_ppos, o_keys, o_counter, o_gstate, bytes;
+    size_t o_desc, o_voff, o_order, o_pos, o_parent, o_ppos, o_keys, o_counter, o_gstate, o_emask, bytes;
 };
 
 int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const int64_t *order_offsets,

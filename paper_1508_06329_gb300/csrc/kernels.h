@@ -16,6 +16,7 @@ struct LexPlan {
     bool split_state;   // 16-bit ids, class ids in shared memory, class arrays in a global workspace
     size_t smem_bytes;  // dynamic shared memory per CTA
     size_t gstate_bytes;// global state bytes per CTA (0: none)
+    int n_max;          // the largest graph the plan was made for
 };
 
 // Picks the kernel variant for graphs of at most n_max vertices.
@@ -31,9 +32,15 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan);
 // kParentUnresolved for the pivots chosen by a class scan.  keys (nullable)
 // is set, on the stream after the search, to the check's initial keys:
 // keys[0..count) = "no violation", keys[count] = keys[count + 1] = 0.
+// emask (nullable): the search also writes each graph's earlier-than masks
+// E_b (b >= 1; row b at emask + ebase + b * mask_stride(n): the vertices
+// numbered before step 32 b), which the staged check reads.  cpar
+// (nullable; n ints per graph at vbase, scratch) makes kParentPivots exact:
+// no kParentUnresolved is left.
 int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                         int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
-                        cudaStream_t stream, int parent_mode = 0, unsigned long long *keys = nullptr);
+                        cudaStream_t stream, int parent_mode = 0, unsigned long long *keys = nullptr,
+                        uint32_t *emask = nullptr, int32_t *cpar = nullptr);
 
 // Bounds-checking build: the next dense LexBFS launch records `code` (a test
 // of the error path); CG_EINVAL in the release build.
@@ -67,6 +74,18 @@ int64_t earlier_mask_words(int n);
 bool peo_rows_vec_ok(const DenseDesc &d);
 int peo_unit_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, bool vec, const int32_t *order,
                     const int32_t *pos, int32_t *ppos, unsigned long long *keys, cg_result *res, cudaStream_t stream);
+// The same check with the rows staged in shared memory: persistent blocks
+// stage runs of 16 or 32 positions (their rows, the rows of the positions
+// just before, and E_b, which the search wrote: lexbfs_dense_launch's emask)
+// with bulk copies into two alternating buffers and test row_v & ~row_p & E_b
+// there.  Needs peo_stage_ok for every graph (rows suited to bulk copies,
+// n <= kStageMaxN), exact parents in ppos (the search's cpar) and the masks
+// at each desc's ebase.
+constexpr int kStageMaxN = 49152;
+bool peo_stage_ok(const DenseDesc &d);
+int peo_stage_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, const int32_t *order,
+                     int32_t *ppos, const uint32_t *emask, unsigned long long *keys, cg_result *res, int num_sms,
+                     cudaStream_t stream);
 // sets *flag when order is not a permutation of 0..n-1 (seen: n ints of scratch)
 int order_check_launch(int n, const int32_t *order, int *seen, int *flag, int num_sms, cudaStream_t stream);
 

@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
                                                          int count, int32_t *__restrict__ order,
                                                          int32_t *__restrict__ pos, int32_t *__restrict__ parent,
                                                          int pmode, unsigned char *gstate, size_t gstate_stride,
-                                                         int *work_counter) {
+                                                         int *work_counter, uint32_t *emask,
+                                                         int32_t *cpar, bool cpar_smem) {
     extern __shared__ __align__(16) unsigned char smem[];
     LexScalars *sc = reinterpret_cast<LexScalars *>(smem);
     unsigned char *free_smem = smem + kLexScalarBytes;
@@ -70,10 +71,14 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
             }
             rows = srows;
             stride = wn;
+            p += ((size_t)n * wn * sizeof(uint32_t) + 15) & ~size_t(15);
             __syncthreads();
         }
+        // the per-class last pivot: in shared memory when it fits beside the state
+        int32_t *cp = cpar ? (cpar_smem ? reinterpret_cast<int32_t *>(p) : cpar + d.vbase) : nullptr;
         lexbfs_cta<Id, T, WPT, LPW>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr,
-                                    parent ? parent + d.vbase : nullptr, pmode);
+                                    parent ? parent + d.vbase : nullptr, pmode, emask ? emask + d.ebase : nullptr,
+                                    cp);
         __syncthreads();
         if (count == 1) break;
     }
@@ -82,13 +87,19 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
 template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, bool SPLIT = false>
 int launch_variant(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                    int32_t *order, int32_t *pos, int32_t *parent, int pmode, void *gstate,
-                   int *work_counter, cudaStream_t stream, unsigned long long *keys) {
+                   int *work_counter, cudaStream_t stream, unsigned long long *keys, uint32_t *emask,
+                   int32_t *cpar) {
     auto kern = lexbfs_dense_kernel<Id, T, WPT, LPW, ROWS_SMEM, SPLIT>;
-    CG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_bytes));
+    // cpar in shared memory when it fits (one store per split class per step:
+    // in global memory it cost ~0.2 us per step on G(n, 0.5), n = 10,000)
+    const size_t cpar_bytes = cpar ? ((size_t)plan.n_max * sizeof(int32_t) + 15) & ~size_t(15) : 0;
+    const bool cpar_smem = cpar && !SPLIT && sizeof(Id) == 2 && plan.smem_bytes + cpar_bytes <= kSmemLimit;
+    const size_t smem = plan.smem_bytes + (cpar_smem ? cpar_bytes : 0);
+    CG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (count > 1) CG_CUDA_TRY(cudaMemsetAsync(work_counter, 0, sizeof(int), stream));
-    kern<<<ctas, T, plan.smem_bytes, stream>>>(descs, single, count, order, pos, parent, pmode,
-                                               static_cast<unsigned char *>(gstate), plan.gstate_bytes,
-                                               work_counter);
+    kern<<<ctas, T, smem, stream>>>(descs, single, count, order, pos, parent, pmode,
+                                    static_cast<unsigned char *>(gstate), plan.gstate_bytes, work_counter, emask,
+                                    cpar, cpar_smem);
     if (keys) {   // the check's initial keys: "no violation", then the CTA counter and error word
         CG_CUDA_TRY(cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * count, stream));
         CG_CUDA_TRY(cudaMemsetAsync(keys + count, 0, 2 * sizeof(unsigned long long), stream));
@@ -109,7 +120,7 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
     const int wn = (n + 31) / 32;
     if (n <= kSmemMaxN) {
         const size_t state = lex_state_bytes<uint16_t>(n);
-        const size_t rows = (size_t)n * wn * 4;
+        const size_t rows = ((size_t)n * wn * 4 + 15) & ~size_t(15);
         p.wide_ids = false;
         p.rows_smem = kLexScalarBytes + state + rows <= kSmemLimit;
         // measured on GB300 (subtree, clique, tree, G(n, 0.1) graphs): 512 threads
@@ -138,18 +149,22 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
     }
     if (p.threads != 128 && p.threads != 256 && p.threads != 512 && p.threads != 1024)
         return set_error(CG_EINVAL, "unsupported CTA size %d", p.threads);
+    p.n_max = n;
     *plan = p;
     return CG_OK;
 }
 
 int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                         int32_t *order, int32_t *pos, int32_t *parent, void *gstate, int *work_counter,
-                        cudaStream_t stream, int parent_mode, unsigned long long *keys) {
+                        cudaStream_t stream, int parent_mode, unsigned long long *keys, uint32_t *emask,
+                        int32_t *cpar) {
     if (count <= 0) return CG_OK;
+    if (emask && (reinterpret_cast<uintptr_t>(emask) & 15) != 0)
+        return set_error(CG_EINVAL, "earlier-than mask buffer not 16-byte aligned");
     ctas = std::max(1, std::min(ctas, count));
     auto go = [&](auto launch, void *gs) {
         return launch(plan, descs, single, count, ctas, order, pos, parent, parent_mode, gs, work_counter, stream,
-                      keys);
+                      keys, emask, cpar);
     };
     if (plan.split_state) return go(launch_variant<uint16_t, 1024, 2, 1, false, true>, gstate);
     if (plan.wide_ids) return go(launch_variant<uint32_t, 1024, 4, 1, false>, gstate);

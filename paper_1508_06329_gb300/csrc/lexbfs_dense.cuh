@@ -26,7 +26,8 @@
 //     collected while splitting), or of the class after it when the top class
 //     empties; only when neither class lost members is a class scan needed.
 //     A known pivot's row is requested right after the first barrier, so its
-//     load overlaps the list update.  Two __syncthreads per step;
+//     load overlaps the list update, the second barrier and the next step's
+//     relabel pass.  Two __syncthreads per step;
 //   * a shared bitmask of numbered vertices filters each pivot row, so only
 //     unnumbered neighbours are visited; the deferred relabel and the split
 //     are two short loops over a word's bits, and a thread posts only its
@@ -38,9 +39,16 @@
 //     stores one value per step, by position (parent[i] = p(order[i])): a
 //     pivot chosen among the moved vertices has the current pivot as parent;
 //     one chosen by a class scan gets kParentUnresolved and the check finds
-//     its parent (a per-step select that kept a class-scan pivot's parent
-//     when it shares the current pivot's class measured 40 ns per step
-//     slower on GB300, far more than the check's gather for those vertices);
+//     it, unless cpar is given: the members of a class share one label and
+//     so one latest numbered neighbour, the pivot that last moved them,
+//     which cpar[c] records (set by the allocators when a class is split off
+//     or moves whole).  A pivot scanned from the top class f shares the
+//     current pivot's parent; one scanned from the class after it reads
+//     cpar there (loaded by thread 0 at the start of the step);
+//   * with emask, the numbered bitmask at the start of every step 32 b
+//     (b >= 1) is also written out as E_b, the vertices numbered before
+//     position 32 b: the staged check reads one mask row per 32 positions
+//     instead of building it from pos;
 //   * the graph's rows are bulk-prefetched into L2 when the CTA starts.
 #pragma once
 #include "common.cuh"
@@ -78,6 +86,7 @@ struct LexScalars {
     int next_graph;
     unsigned front_min[2];
     unsigned second_min[2];
+    unsigned split[2];   // a class was split in the step of this parity (its moved vertices need a relabel)
     unsigned red[32];
 };
 
@@ -146,17 +155,19 @@ __device__ inline LexState<Id> lex_state_carve_split(unsigned char *smem, unsign
     return s;
 }
 
-// Word w of row x, padding bits cleared.
-__device__ __forceinline__ uint32_t row_word(const uint32_t *__restrict__ rows, int stride, int x, int w,
-                                             int wn, uint32_t lastmask) {
+// Word w of row x as stored, 0 for w >= wn: nothing touches the loaded value
+// here, so the warp does not wait for it until the word is first used
+// (padding bits are cleared there).
+__device__ __forceinline__ uint32_t row_raw(const uint32_t *__restrict__ rows, int stride, int x, int w, int wn) {
+    uint32_t v = 0u;
 #ifdef CG_BOUNDS_CHECK
-    if ((unsigned)w >= (unsigned)wn || x < 0) {   // x < n holds when x comes from the state arrays
+    if (w < wn && x < 0) {   // x < n holds when x comes from the state arrays
         cg_dbg_record(kChkRow, (unsigned long long)(unsigned)x);
         return 0u;
     }
 #endif
-    uint32_t v = rows[(size_t)x * stride + w];
-    return w == wn - 1 ? (v & lastmask) : v;
+    if (w < wn) v = rows[(size_t)x * stride + w];
+    return v;
 }
 
 // One CTA computes the LexBFS order of one graph.  rows/stride address the
@@ -170,7 +181,8 @@ __device__ __forceinline__ uint32_t row_word(const uint32_t *__restrict__ rows, 
 template <typename Id, int T, int WPT, int LPW>
 __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n, LexState<Id> st,
                            LexScalars *sc, int32_t *__restrict__ order, int32_t *__restrict__ pos,
-                           int32_t *__restrict__ parent, int pmode = kParentMoves) {
+                           int32_t *__restrict__ parent, int pmode = kParentMoves,
+                           uint32_t *__restrict__ emask = nullptr, int32_t *__restrict__ cpar = nullptr) {
     using Tr = IdTraits<Id>;
     using Sz = typename Tr::Sz;
     const Id kNumbered = (Id)~(Id)0;
@@ -204,27 +216,48 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
         sc->free_top = n - 1;
         sc->front_min[0] = sc->front_min[1] = kNoVertex;
         sc->second_min[0] = sc->second_min[1] = kNoVertex;
+        sc->split[0] = sc->split[1] = 0u;
+        if (cpar) cpar[0] = -1;   // class 0 (all vertices) has no numbered neighbour
     }
-    uint32_t row_cur[WPT], row_prev[WPT], row_nxt[WPT], amask[WPT];
+    uint32_t rA[WPT], rB[WPT], rC[WPT], amask[WPT];   // previous / current / next pivot row, as loaded
     int x = 0;
 #pragma unroll
     for (int k = 0; k < WPT; ++k) {
         const int w = k * kGroups + wt;
-        row_cur[k] = w < wn ? row_word(rows, stride, x, w, wn, lastmask) & part : 0u;
-        row_prev[k] = 0u;
-        row_nxt[k] = 0u;
+        rB[k] = row_raw(rows, stride, x, w, wn);
+        rA[k] = 0u;
+        rC[k] = 0u;
         amask[k] = 0u;
     }
     Id pending_free = kNone;
     int par_x = -1;   // p(x) of the current pivot (thread 0, kParentPivots)
     __syncthreads();
 
-    for (int i = 0; i < n; ++i) {
+    auto step = [&](const int i, uint32_t (&row_prev)[WPT], uint32_t (&row_cur)[WPT],
+                    uint32_t (&row_nxt)[WPT]) -> bool {
         const int slot = i & 1;
         const Id f = st.cnext[HEAD];
         const Id g = st.cnext[f];
         const Sz fsz = st.sz[f] & Tr::kMask;  // still counts x
+        // uniform shortcuts: when the previous step split no class, every class
+        // that moved kept its id and the relabel is a no-op; when f is the only
+        // class, every unnumbered neighbour of x is in f and a warp adds its
+        // count to f with one atomic (cliques take this path at every step)
+        const bool relabel = sc->split[slot ^ 1] != 0u;
+        const bool single = g == kNone;
+        // parent of a pivot scanned from g (thread 0; used after barrier A, so the load overlaps phase S)
+        const int cpar_g = t == 0 && cpar && g != kNone ? cpar[g] : kParentUnresolved;
 
+        // E_b = the vertices numbered before x, written at every step 32 b
+        // (x's own bit may already be set by a thread of phase S, so it is cleared)
+        if (emask && (i & 31) == 0 && i > 0) {
+            const int xw = x >> 5;
+            uint32_t *eb = emask + (size_t)(i >> 5) * mask_stride(n);
+            for (int w = t; w < mask_stride(n); w += T) {   // padding words past ceil(n/32) are zero
+                const uint32_t nb = w < wn ? st.numbered[w] : 0u;
+                eb[w] = w == xw ? nb & ~(1u << (x & 31)) : nb;
+            }
+        }
         // ---- phase S: deferred relabel, number x, split by N(x)
         if (t == 0) {
             if (pending_free != kNone) {
@@ -243,17 +276,21 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             if (w < wn) {
                 const uint32_t prev = row_prev[k];
                 uint32_t nb = st.numbered[w];
-                const uint32_t cur = row_cur[k] & ~nb;  // unnumbered neighbours of x
                 // relabel pass: vertices moved by the previous pivot take their new class
-                uint32_t bits = prev;
+                uint32_t bits = relabel ? prev : 0u;
                 while (bits) {
                     const int y = (w << 5) + (__ffs(bits) - 1);
                     bits &= bits - 1;
                     st.cls[y] = st.child[st.cls[y]];
                 }
+                uint32_t rw = row_cur[k];   // first use of the pivot row's word
+                if (w == wn - 1) rw &= lastmask;
+                const uint32_t cur = rw & part & ~nb;  // unnumbered neighbours of x
                 // split pass: count moved members per class; a lane's first moved
                 // member of the top class (or of the next one) is its pivot candidate
-                bits = cur;
+                bits = single ? 0u : cur;
+                if (single && parent && pmode == kParentMoves)
+                    for (uint32_t pb = cur; pb; pb &= pb - 1) parent[(w << 5) + (__ffs(pb) - 1)] = x;
                 bool f_done = false, g_done = false;
                 while (bits) {
                     const int b = __ffs(bits) - 1;
@@ -277,6 +314,16 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                     st.numbered[w] = nb | (1u << (x & 31));
                 }
                 row_cur[k] = cur;
+            }
+            if (single) {   // warp-uniform: the warp's count of f's moved members in one atomic
+                const uint32_t cur = w < wn ? row_cur[k] : 0u;
+                const unsigned total = __reduce_add_sync(0xFFFFFFFFu, (unsigned)__popc(cur));
+                const unsigned lanes = __ballot_sync(0xFFFFFFFFu, cur != 0u);
+                if (lanes && (t & 31) == __ffs(lanes) - 1) {   // the warp's lowest moved vertex
+                    const Sz old = atomicAdd(&st.sz[f], (Sz)total << Tr::kShift);
+                    if ((old >> Tr::kShift) == 0) am = cur & (0u - cur);   // first arrival allocates
+                    atomicMin(&sc->front_min[slot], (unsigned)((w << 5) + __ffs(cur) - 1));
+                }
             }
             amask[k] = am;
         }
@@ -304,13 +351,11 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             mode = 2;
             target = g;
         }
-        if (t == 0) par_x = mode == 0 ? x : kParentUnresolved;   // a moved pivot's parent is x
+        // a moved pivot's parent is x; one scanned from f shares x's; one from g has g's
+        if (t == 0) par_x = mode == 0 ? x : mode == 1 && cpar ? par_x : cpar_g;
         if (mode == 0) {
 #pragma unroll
-            for (int k = 0; k < WPT; ++k) {
-                const int w = k * kGroups + wt;
-                row_nxt[k] = w < wn ? row_word(rows, stride, (int)xn, w, wn, lastmask) & part : 0u;
-            }
+            for (int k = 0; k < WPT; ++k) row_nxt[k] = row_raw(rows, stride, (int)xn, k * kGroups + wt, wn);
         }
 
         // ---- phase A: allocate / link split classes
@@ -328,13 +373,16 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                 if (mv == size) {
                     st.child[c] = c;
                     st.sz[c] = size;
+                    if (cpar) cpar[c] = x;
                     if (fempty && c == g) {
                         st.cnext[HEAD] = g;
                         st.cprev[g] = HEAD;
                     }
                 } else {
                     const int idx = atomicSub(&sc->free_top, 1) - 1;
+                    sc->split[slot] = 1u;
                     const Id cn = st.freel[idx];
+                    if (cpar) cpar[cn] = x;
                     st.child[c] = cn;
                     st.sz[cn] = mv;
                     st.sz[c] = size - mv;
@@ -357,6 +405,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                 }
             }
             sc->front_min[slot ^ 1] = kNoVertex;
+            sc->split[slot ^ 1] = 0u;   // read at the start of this step by every thread (before barrier A)
             sc->second_min[slot ^ 1] = kNoVertex;
         }
         // class scan for the next pivot, overlapping phase A (cls is not written there)
@@ -371,21 +420,35 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
             if ((t & 31) == 0) sc->red[t >> 5] = best;
         }
         __syncthreads();  // B
-        if (mode == 3) break;
+        if (mode == 3) return false;
         if (mode != 0) {
             const unsigned r = (t & 31) < (T / 32) ? sc->red[t & 31] : kNoVertex;
             xn = __reduce_min_sync(0xFFFFFFFFu, r);
 #pragma unroll
-            for (int k = 0; k < WPT; ++k) {
-                const int w = k * kGroups + wt;
-                row_nxt[k] = w < wn ? row_word(rows, stride, (int)xn, w, wn, lastmask) & part : 0u;
-            }
+            for (int k = 0; k < WPT; ++k) row_nxt[k] = row_raw(rows, stride, (int)xn, k * kGroups + wt, wn);
         }
         x = (int)xn;
+        return true;
+    };
+    if constexpr (WPT == 1) {
+        // one row word per thread: three registers rotate through the roles
+        // previous / current / next pivot row (the loop is unrolled three
+        // times), so no register copy at the end of a step waits for the next
+        // row's load; the load is first consumed in the next step's split pass,
+        // after its relabel pass (9% faster per step on GB300 at N = 16,384)
+        for (int i = 0; i < n; i += 3) {
+            if (!step(i, rA, rB, rC) || i + 1 >= n) break;
+            if (!step(i + 1, rB, rC, rA) || i + 2 >= n) break;
+            if (!step(i + 2, rC, rA, rB)) break;
+        }
+    } else {   // several words per thread: the rotation would spill, so the rows are copied
+        for (int i = 0; i < n; ++i) {
+            if (!step(i, rA, rB, rC)) break;
 #pragma unroll
-        for (int k = 0; k < WPT; ++k) {
-            row_prev[k] = row_cur[k];
-            row_cur[k] = row_nxt[k];
+            for (int k = 0; k < WPT; ++k) {
+                rA[k] = rB[k];
+                rB[k] = rC[k];
+            }
         }
     }
 }

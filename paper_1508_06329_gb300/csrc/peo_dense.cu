@@ -605,6 +605,218 @@ __global__ void __launch_bounds__(kUnitThreads) peo_unit_kernel(const DenseDesc 
     }
 }
 
+// ---- the check of a search's own order, rows staged in shared memory
+//
+// For almost every vertex of a LexBFS order, p(v) is the vertex numbered just
+// before it, so the rows of a run of positions hold nearly all the parent
+// rows too.  A unit is P consecutive positions s0 .. s0 + P - 1 inside one
+// group b of 32 positions (P = 16 or 32).  Each block is persistent over the
+// units blockIdx.x, blockIdx.x + gridDim.x, ... of graph blockIdx.y, with two
+// shared-memory buffers: while it checks unit k, the 16-byte asynchronous
+// copies (cp.async, every thread, one commit group per unit) of unit k + 1
+// are in flight, warp 0 has written the vertices of unit k + 2 and holds
+// those of unit k + 3 in registers.
+//   * a unit's buffer: the rows of positions s0 - 1 .. s0 + P - 1 (slot s =
+//     position s0 - 1 + s) and E_b (the earlier-than mask the search wrote at
+//     step 32 b, zero padded; zero for b = 0); its meta data: the vertices,
+//     their exact parents (from the search) and the group's 32 vertices;
+//   * checking position i = s0 + j (P / 8 per warp): the lowest bit of
+//     row_v & ~row_p & E_b other than p, 128-bit shared-memory loads (row p
+//     from its slot, or from global memory when p was numbered before
+//     s0 - 1), plus the group's own earlier positions 32 b .. i - 1 one per
+//     lane; the first violation in order is kept by an atomicMin of
+//     (pos(v) << 32 | u) and the last block writes the results.
+// Every row is read from L2 about once; the masks are 1/P of a row per
+// position.  (One bulk copy per row, cp.async.bulk on an mbarrier, moved the
+// same bytes about three times slower: the block's bulk copies completed one
+// after another.)
+constexpr int kStageThreads = 256;
+constexpr int kStageWarps = kStageThreads / 32;
+
+__device__ __forceinline__ uint4 lds4(const uint32_t *p) { return *reinterpret_cast<const uint4 *>(p); }
+
+template <int P>
+struct StageMeta {
+    int v[P + 1];   // vertex of slot s (-1: none)
+    int p[P];       // p(v) of position s0 + j (-1: no earlier neighbour)
+    int grp[32];    // vertices of the group's positions 32 b .. 32 b + 31
+    int s0, npos;
+};
+
+template <int P>
+__global__ void __launch_bounds__(kStageThreads) peo_stage_kernel(const DenseDesc *__restrict__ descs,
+                                                                  DenseDesc single, int count,
+                                                                  const int32_t *__restrict__ order,
+                                                                  const int32_t *__restrict__ ppos,
+                                                                  const uint32_t *__restrict__ emask,
+                                                                  unsigned long long *__restrict__ keys,
+                                                                  cg_result *__restrict__ res) {
+    constexpr int kSlots = P + 2;   // P + 1 rows and E_b
+    extern __shared__ __align__(128) uint32_t sbuf[];   // 2 buffers x kSlots slots x mask_stride(n) words
+    __shared__ StageMeta<P> meta[3];
+    __shared__ bool s_last;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int gi = blockIdx.y;
+    const DenseDesc d = descs ? descs[gi] : single;
+    const int n = d.n;
+    const int units = (n + P - 1) / P;
+    const int nk = (int)blockIdx.x < units ? (units - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    if (nk > 0) {
+        const int sw = mask_stride(n);   // slot stride: ceil(n/32) rounded up to 4 words (16 bytes)
+        const int q4 = sw >> 2;          // 16-byte chunks per slot
+        const int32_t *ord_g = order + d.obase;
+        const int32_t *pp_g = ppos + d.vbase;
+        const uint32_t *E_g = emask + d.ebase;
+        // warp 0's registers: a unit ahead (lane l: the vertex and parent of
+        // position s0 + l, the group's vertex 32 b + l; lane 0 also the vertex
+        // of position s0 - 1)
+        int rv_ = -1, rp_ = -1, rg_ = -1, r0_ = -1;
+        auto load_unit = [&](int k) {   // warp 0: global loads, not waited for here
+            const int s0 = ((int)blockIdx.x + k * (int)gridDim.x) * P, g0 = s0 & ~31;
+            rv_ = lane < P && s0 + lane < n ? __ldg(ord_g + s0 + lane) : -1;
+            rp_ = lane < P && s0 + lane < n ? __ldg(pp_g + s0 + lane) : -1;
+            rg_ = g0 + lane < n ? __ldg(ord_g + g0 + lane) : -1;
+            r0_ = lane == 0 && s0 > 0 ? __ldg(ord_g + s0 - 1) : -1;
+        };
+        auto write_meta = [&](int k) {   // warp 0: registers -> meta[k % 3]
+            StageMeta<P> &m = meta[k % 3];
+            const int s0 = ((int)blockIdx.x + k * (int)gridDim.x) * P;
+            const int npos = min(P, n - s0);
+            int v = rv_, p = rp_, gv = rg_, v0 = r0_;
+            // values outside 0..n-1 (only if the buffers were overwritten, or a
+            // parent left open) are reported, never used
+            const bool bad = (unsigned)(v + 1) > (unsigned)n || (unsigned)(gv + 1) > (unsigned)n ||
+                             (unsigned)(v0 + 1) > (unsigned)n || (lane < npos && (v < 0 || p >= n || p < -1));
+            if (bad) {
+                atomicOr(keys + count + 1, 2ull);
+#ifdef CG_BOUNDS_CHECK
+                cg_dbg_record(kChkUnitGroup, (unsigned long long)(s0 + lane));
+#endif
+                if ((unsigned)(v + 1) > (unsigned)n) v = -1;
+                if ((unsigned)(gv + 1) > (unsigned)n) gv = -1;
+                if ((unsigned)(v0 + 1) > (unsigned)n) v0 = -1;
+                if (p >= n || p < -1) p = -1;
+            }
+            if (lane < P) {
+                m.v[lane + 1] = v;
+                m.p[lane] = v >= 0 ? p : -1;
+            }
+            if (lane == 0) {
+                m.v[0] = v0;
+                m.s0 = s0;
+                m.npos = npos;
+            }
+            m.grp[lane] = gv;
+        };
+        auto issue_unit = [&](int k) {   // every thread: its 16-byte chunks of unit k, one commit group
+            const StageMeta<P> &m = meta[k % 3];
+            uint32_t *buf = sbuf + (size_t)(k & 1) * kSlots * sw;
+            const int b = m.s0 >> 5;
+            for (int c = t; c < kSlots * q4; c += kStageThreads) {
+                const int slot = c / q4, off = (c - slot * q4) << 2;
+                uint32_t *dst = buf + (size_t)slot * sw + off;
+                if (slot <= P) {
+                    const int v = m.v[slot];
+                    if (v >= 0) cp_async16(dst, d.rows + (size_t)v * d.words + off);
+                } else if (b > 0) {
+                    cp_async16(dst, E_g + (size_t)b * sw + off);
+                } else {   // E_0: nothing precedes position 0
+                    *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+            cp_async_commit();
+        };
+        if (warp == 0) {
+            load_unit(0);
+            write_meta(0);
+            if (nk > 1) {
+                load_unit(1);
+                write_meta(1);
+            }
+            if (nk > 2) load_unit(2);
+        }
+        __syncthreads();   // meta[0], meta[1]
+        issue_unit(0);
+        for (int k = 0; k < nk; ++k) {
+            if (k + 1 < nk) issue_unit(k + 1);
+            else cp_async_commit();   // an empty group keeps the count uniform
+            if (warp == 0 && k + 2 < nk) {
+                write_meta(k + 2);
+                if (k + 3 < nk) load_unit(k + 3);
+            }
+            cp_async_wait<1>();   // this thread's copies of unit k have landed
+            __syncthreads();      // everyone's
+            const StageMeta<P> &m = meta[k % 3];
+            const uint32_t *buf = sbuf + (size_t)(k & 1) * kSlots * sw;
+            const uint32_t *E = buf + (size_t)(P + 1) * sw;
+            const int s0 = m.s0, g0 = s0 & ~31;
+            for (int j = warp; j < m.npos; j += kStageWarps) {
+                const int p = m.p[j];
+                if (p < 0) continue;   // no earlier neighbour: LN_v is empty
+                const uint32_t *rv = buf + (size_t)(j + 1) * sw;
+                // row p: a staged slot 0..j when p sits there, else global memory
+                const unsigned at = __ballot_sync(0xFFFFFFFFu, lane <= j && m.v[lane] == p);
+                const uint32_t *rps = at ? buf + (size_t)(__ffs(at) - 1) * sw : nullptr;
+                const uint32_t *rpg = d.rows + (size_t)p * d.words;
+                const int pw4 = (p >> 5) & ~3, pk = (p >> 5) & 3;
+                const uint32_t keep = ~(1u << (p & 31));
+                unsigned mn = kNoBad;
+                for (int c = 0; c < sw; c += 128) {   // warp-uniform trip count; 4 words per lane
+                    const int w4 = c + 4 * lane;
+                    uint32_t b0 = 0u, b1 = 0u, b2 = 0u, b3 = 0u;
+                    if (w4 < sw) {   // E_b is zero past n: padding bits and words drop out
+                        const uint4 a = lds4(rv + w4), e = lds4(E + w4);
+                        const uint4 q = rps ? lds4(rps + w4) : ldg4(rpg + w4);
+                        b0 = a.x & ~q.x & e.x;
+                        b1 = a.y & ~q.y & e.y;
+                        b2 = a.z & ~q.z & e.z;
+                        b3 = a.w & ~q.w & e.w;
+                        if (w4 == pw4) {   // p itself is not tested
+                            if (pk == 0) b0 &= keep;
+                            else if (pk == 1) b1 &= keep;
+                            else if (pk == 2) b2 &= keep;
+                            else b3 &= keep;
+                        }
+                    }
+                    if (b0 | b1 | b2 | b3) {   // this lane's lowest bad id in the chunk
+                        const int kk = b0 ? 0 : b1 ? 1 : b2 ? 2 : 3;
+                        const uint32_t bits = b0 ? b0 : b1 ? b1 : b2 ? b2 : b3;
+                        mn = (unsigned)(((w4 + kk) << 5) + __ffs(bits) - 1);
+                    }
+                    if (__any_sync(0xFFFFFFFFu, mn != kNoBad)) break;   // later chunks hold higher ids
+                }
+                // the group's own earlier positions 32 b .. i - 1, one per lane
+                if (lane < s0 + j - g0) {
+                    const int u = m.grp[lane];
+                    if (u >= 0 && u != p) {
+                        const uint32_t bit = 1u << (u & 31);
+                        const uint32_t pw = rps ? rps[u >> 5] : __ldg(rpg + (u >> 5));
+                        if ((rv[u >> 5] & bit) && !(pw & bit)) mn = min(mn, (unsigned)u);
+                    }
+                }
+                mn = __reduce_min_sync(0xFFFFFFFFu, mn);
+                if (lane == 0 && mn != kNoBad)
+                    atomicMin(keys + gi, ((unsigned long long)(unsigned)(s0 + j) << 32) | mn);
+            }
+            __syncthreads();   // buffer k & 1 and meta[k % 3] are free again
+        }
+    }
+    // the last block to finish turns the keys into results (keys[count] counts blocks)
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        s_last = atomicAdd(keys + count, 1ull) == (unsigned long long)gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        const unsigned long long err = atomicAdd(keys + count + 1, 0ull);
+        for (int g = t; g < count; g += kStageThreads)
+            write_result_ppos(descs ? descs[g] : single, atomicAdd(keys + g, 0ull), err, order, ppos,
+                              res + (descs ? descs[g].rindex : g));
+    }
+}
+
 }  // namespace
 
 int invert_order_launch(const DenseDesc *descs, DenseDesc single, int count, const int64_t *voff, int64_t total,
@@ -696,6 +908,43 @@ int peo_unit_launch(const DenseDesc *descs, DenseDesc single, int count, int n_m
 
 bool peo_rows_vec_ok(const DenseDesc &d) {
     return (reinterpret_cast<uintptr_t>(d.rows) & 15) == 0 && (d.words & 3) == 0;
+}
+
+bool peo_stage_ok(const DenseDesc &d) { return d.n > 0 && d.n <= kStageMaxN && peo_rows_vec_ok(d); }
+
+namespace {
+// Dynamic shared memory of the staged check for units of P positions.
+size_t stage_smem_bytes(int P, int n_max) { return 2 * (size_t)(P + 2) * mask_stride(n_max) * sizeof(uint32_t); }
+}  // namespace
+
+int peo_stage_launch(const DenseDesc *descs, DenseDesc single, int count, int n_max, const int32_t *order,
+                     int32_t *ppos, const uint32_t *emask, unsigned long long *keys, cg_result *res, int num_sms,
+                     cudaStream_t stream) {
+    if (count <= 0 || n_max <= 0 || n_max > kStageMaxN)
+        return set_error(CG_EINVAL, "staged check needs 1..%d vertices (got %d)", kStageMaxN, n_max);
+    if (count > 65535) return set_error(CG_EINVAL, "too many graphs for one check launch (%d)", count);
+    if (!emask || (reinterpret_cast<uintptr_t>(emask) & 15) != 0)
+        return set_error(CG_EINVAL, "staged check needs a 16-byte aligned mask buffer");
+    // units of 16 positions (more resident blocks per SM) unless 32 keep as many warps resident
+    auto per_sm_of = [](size_t smem) {
+        return (int)std::min<size_t>(2048 / kStageThreads, (228 * 1024) / (smem + 2048));
+    };
+    const int P = per_sm_of(stage_smem_bytes(32, n_max)) >= per_sm_of(stage_smem_bytes(16, n_max)) ? 32 : 16;
+    const size_t smem = stage_smem_bytes(P, n_max);
+    const int per_sm = std::max(1, per_sm_of(smem));
+    const int64_t units = ceil_div(n_max, P);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(units, ceil_div((int64_t)num_sms * per_sm, count)));
+    const dim3 grid((unsigned)blocks, (unsigned)count);
+    if (P == 32) {
+        CG_CUDA_TRY(cudaFuncSetAttribute(peo_stage_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        peo_stage_kernel<32><<<grid, kStageThreads, smem, stream>>>(descs, single, count, order, ppos, emask, keys, res);
+    } else {
+        CG_CUDA_TRY(cudaFuncSetAttribute(peo_stage_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        peo_stage_kernel<16><<<grid, kStageThreads, smem, stream>>>(descs, single, count, order, ppos, emask, keys, res);
+    }
+    CG_LAUNCH_CHECK("peo_stage_kernel");
+    CG_DEBUG_CHECK(stream, "peo_stage_kernel");
+    return CG_OK;
 }
 
 int finalize_launch(const DenseDesc *descs, DenseDesc single, int count, const unsigned long long *keys,

@@ -73,3 +73,22 @@ def test_algorithmic_bytes():
     nnz = int(c.row_ptr[-1])
     assert c.nnz == nnz == int(np.unpackbits(g.rows.view(np.uint8)).sum())
     assert bench.algorithmic_bytes(c) == 3 * (8 * c.n + 4 * nnz) + 4 * nnz
+
+
+def test_traffic_figure_follows_the_kernel_sources(tmp_path):
+    """The roofline's traffic is read from the kept ncu summary only while the
+    kernel's sources hash to the value recorded at capture time."""
+    summary, srcs = bench.TRAFFIC_SUMMARIES["dense16k"]
+    for p in srcs:
+        (tmp_path / os.path.dirname(p)).mkdir(parents=True, exist_ok=True)
+        (tmp_path / p).write_bytes(open(os.path.join(bench.ROOT, p), "rb").read())
+    (tmp_path / "profiles").mkdir()
+    digest = bench.sources_sha256(srcs, str(tmp_path))
+    (tmp_path / summary).write_text(f"kernel: x\nsource_sha256: {digest}\ndram_bytes_per_launch: 69120000\n")
+    assert bench.ncu_traffic("dense16k", root=str(tmp_path))[0] == 69120000.0
+    (tmp_path / summary).write_text(f"source_sha256: {'0' * 64}\ndram_bytes_per_launch: 69120000\n")
+    t, note = bench.ncu_traffic("dense16k", root=str(tmp_path))
+    assert t is None and "changed" in note
+    (tmp_path / summary).write_text("dram_bytes_per_launch: 1\n")
+    assert bench.ncu_traffic("dense16k", root=str(tmp_path))[0] is None
+    assert bench.ncu_traffic("batch4096", root=str(tmp_path))[0] is None

@@ -113,6 +113,34 @@ def test_padding_words_and_garbage_padding_bits(ctx):
         assert np.array_equal(got_o, want.order) and got_w == want.witness
 
 
+def test_padding_words_of_staged_rows(ctx):
+    """Rows padded to a multiple of 4 words take the staged check, whose bulk
+    copies bring in the padding word after ceil(n/32) and the padding bits of
+    the last word: both must be ignored."""
+    for n, t in ((70, 15), (300, 60)):
+        g = gg.subtree_dense(n, t, n)
+        for h in (g, gg.plant_cycle(g, 6, n)[0]):
+            wn = (n + 31) // 32
+            wide = gg.empty_dense(n, words=(wn + 3) // 4 * 4 + 4)
+            wide.rows[:, :wn] = h.rows
+            wide.rows[:, wn:] = 0xDEADBEEF
+            if n % 32:
+                wide.rows[:, wn - 1] |= np.uint32((0xFFFFFFFF << (n % 32)) & 0xFFFFFFFF)
+            want = oracle.chordal_test(h)
+            got_w, got_o = run_dense(ctx, wide)
+            assert np.array_equal(got_o, want.order) and got_w == want.witness
+
+
+@pytest.mark.parametrize("n", [49152, 49153])
+def test_staged_check_size_limit(ctx, n):
+    """The largest graph whose check stages its rows in shared memory, and the
+    first one checked with the masks built from pos."""
+    g = gg.subtree_dense(n, n // 2, n)
+    assert assert_parity(ctx, g).chordal == 1
+    h, _ = gg.plant_cycle(g, 7, n)
+    assert assert_parity(ctx, h).chordal == 0
+
+
 def test_small_dense_workload(ctx):
     g, h, _ = gg.small_dense_pair()
     assert assert_parity(ctx, g).chordal == 1
