@@ -61,63 +61,8 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// ---- bulk copies global -> shared memory (cp.async.bulk, completed on an mbarrier)
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t arrivals) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(arrivals) : "memory");
-}
-
-// Makes shared-memory writes of the generic proxy (and an mbarrier's
-// initialisation) visible to the bulk-copy engine.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// One arrival that also announces `bytes` of bulk-copy data for the phase.
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Copies `bytes` (a multiple of 16; both addresses 16-byte aligned) from
-// global memory into this CTA's shared memory; completion counts on `bar`.
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait_parity(unsigned long long *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Waits for the phase with the given parity to complete; gives up after
-// about `limit_ns` nanoseconds (the global timer) and returns false then.
-__device__ __forceinline__ bool mbar_wait_parity_bounded(unsigned long long *bar, uint32_t parity,
-                                                         unsigned long long limit_ns = 1000000000ull) {
-    const unsigned long long t0 = globaltimer_ns();
-    for (;;) {
-        if (mbar_try_wait_parity(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > limit_ns) return false;
-    }
 }
 
 // ---- per-thread asynchronous copies global -> shared memory (cp.async, 16 bytes,

@@ -712,16 +712,20 @@ __global__ void __launch_bounds__(kStageThreads) peo_stage_kernel(const DenseDes
             const StageMeta<P> &m = meta[k % 3];
             uint32_t *buf = sbuf + (size_t)(k & 1) * kSlots * sw;
             const int b = m.s0 >> 5;
-            for (int c = t; c < kSlots * q4; c += kStageThreads) {
-                const int slot = c / q4, off = (c - slot * q4) << 2;
-                uint32_t *dst = buf + (size_t)slot * sw + off;
+            for (int slot = warp; slot < kSlots; slot += kStageWarps) {   // a warp per slot, a lane per chunk
+                uint32_t *dst = buf + (size_t)slot * sw;
+                const uint32_t *src = nullptr;
                 if (slot <= P) {
                     const int v = m.v[slot];
-                    if (v >= 0) cp_async16(dst, d.rows + (size_t)v * d.words + off);
+                    if (v >= 0) src = d.rows + (size_t)v * d.words;
                 } else if (b > 0) {
-                    cp_async16(dst, E_g + (size_t)b * sw + off);
-                } else {   // E_0: nothing precedes position 0
-                    *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+                    src = E_g + (size_t)b * sw;
+                }
+                if (src) {
+                    for (int c = lane; c < q4; c += 32) cp_async16(dst + 4 * c, src + 4 * c);
+                } else if (slot > P) {   // E_0: nothing precedes position 0
+                    for (int c = lane; c < q4; c += 32)
+                        *reinterpret_cast<uint4 *>(dst + 4 * c) = make_uint4(0u, 0u, 0u, 0u);
                 }
             }
             cp_async_commit();
