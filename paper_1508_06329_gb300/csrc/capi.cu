@@ -34,6 +34,7 @@ const char *cg_debug_array_name(unsigned code) {
         case kChkSize: return "dense LexBFS class size";
         case kChkNumbered: return "dense LexBFS numbered mask";
         case kChkRow: return "dense LexBFS pivot row";
+        case kChkMoved: return "dense LexBFS moved counts";
         case kChkCsrCls: return "CSR LexBFS cls";
         case kChkCsrVnext: return "CSR LexBFS vnext";
         case kChkCsrVprev: return "CSR LexBFS vprev";

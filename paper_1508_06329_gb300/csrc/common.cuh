@@ -138,7 +138,7 @@ __device__ __forceinline__ T *cg_arr(T *p, unsigned long long, unsigned) {
 
 // Array codes of the bounds-checking build (the high byte of the error word).
 enum : unsigned {
-    kChkCls = 1, kChkChild, kChkFree, kChkCnext, kChkCprev, kChkSize, kChkNumbered, kChkRow,
+    kChkCls = 1, kChkChild, kChkFree, kChkCnext, kChkCprev, kChkSize, kChkNumbered, kChkRow, kChkMoved,
     kChkCsrCls = 16, kChkCsrVnext, kChkCsrVprev, kChkCsrCnext, kChkCsrCprev, kChkCsrCfirst, kChkCsrClast,
     kChkCsrCsize, kChkCsrCmoved, kChkCsrCchild, kChkCsrFree, kChkCsrSy, kChkCsrSop, kChkCsrSon, kChkCsrSrun,
     kChkCsrSkey,

@@ -20,7 +20,7 @@ constexpr int kSmemMaxN = 16384;             // 16-bit ids, whole state in share
 constexpr int kSplitMaxN = 65520;            // 16-bit ids, class ids in shared memory, class arrays global
 constexpr int kWideMaxN = 131072;            // 32-bit ids: 4 words per thread at 1024 threads
 
-template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, bool SPLIT = false>
+template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, int SPLIT = 0>
 __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__restrict__ descs, DenseDesc single,
                                                          int count, int32_t *__restrict__ order,
                                                          int32_t *__restrict__ pos, int32_t *__restrict__ parent,
@@ -49,9 +49,9 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
         // where the state lives is fixed per variant at compile time, so every
         // state access compiles to a shared- or a global-memory instruction
         // (a runtime choice leaves generic loads, stores and atomics)
-        if constexpr (SPLIT) {
-            st = lex_state_carve_split<Id>(p, gstate + (size_t)blockIdx.x * gstate_stride, n);
-            p += lex_split_smem_bytes<Id>(n);
+        if constexpr (SPLIT != 0) {   // split layouts 1..3
+            st = lex_state_carve_split<Id, SPLIT>(p, gstate + (size_t)blockIdx.x * gstate_stride, n);
+            p += lex_split_smem_bytes<Id>(n, SPLIT);
         } else if constexpr (sizeof(Id) == 4) {   // 32-bit ids: the whole state in the workspace
             st = lex_state_carve<Id>(gstate + (size_t)blockIdx.x * gstate_stride, n);
         } else {
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
         }
         // the per-class last pivot: in shared memory when it fits beside the state
         int32_t *cp = cpar ? (cpar_smem ? reinterpret_cast<int32_t *>(p) : cpar + d.vbase) : nullptr;
-        lexbfs_cta<Id, T, WPT, LPW>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr,
+        lexbfs_cta<Id, T, WPT, LPW, (SPLIT >= kLayoutSplitMv)>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr,
                                     parent ? parent + d.vbase : nullptr, pmode, emask ? emask + d.ebase : nullptr,
                                     cp);
         __syncthreads();
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
     }
 }
 
-template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, bool SPLIT = false>
+template <typename Id, int T, int WPT, int LPW, bool ROWS_SMEM, int SPLIT = 0>
 int launch_variant(const LexPlan &plan, const DenseDesc *descs, DenseDesc single, int count, int ctas,
                    int32_t *order, int32_t *pos, int32_t *parent, int pmode, void *gstate,
                    int *work_counter, cudaStream_t stream, unsigned long long *keys, uint32_t *emask,
@@ -135,11 +135,17 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
         p.gstate_bytes = 0;
     } else if (n <= kSplitMaxN) {
         p.wide_ids = false;
-        p.split_state = true;
         p.rows_smem = false;
         p.threads = 1024;
-        p.smem_bytes = kLexScalarBytes + lex_split_smem_bytes<uint16_t>(n);
-        p.gstate_bytes = lex_split_global_bytes<uint16_t>(n);
+        // as much of the per-class state in shared memory as fits
+        p.split_state = kLayoutSplit;
+        for (int l = kLayoutSplitMvChild; l > kLayoutSplit; --l)
+            if (kLexScalarBytes + lex_split_smem_bytes<uint16_t>(n, l) <= kSmemLimit) {
+                p.split_state = l;
+                break;
+            }
+        p.smem_bytes = kLexScalarBytes + lex_split_smem_bytes<uint16_t>(n, p.split_state);
+        p.gstate_bytes = lex_split_global_bytes<uint16_t>(n, p.split_state);
     } else {
         p.wide_ids = true;
         p.rows_smem = false;
@@ -166,7 +172,10 @@ int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc s
         return launch(plan, descs, single, count, ctas, order, pos, parent, parent_mode, gs, work_counter, stream,
                       keys, emask, cpar);
     };
-    if (plan.split_state) return go(launch_variant<uint16_t, 1024, 2, 1, false, true>, gstate);
+    if (plan.split_state == kLayoutSplitMvChild)
+        return go(launch_variant<uint16_t, 1024, 2, 1, false, kLayoutSplitMvChild>, gstate);
+    if (plan.split_state == kLayoutSplitMv) return go(launch_variant<uint16_t, 1024, 2, 1, false, kLayoutSplitMv>, gstate);
+    if (plan.split_state) return go(launch_variant<uint16_t, 1024, 2, 1, false, kLayoutSplit>, gstate);
     if (plan.wide_ids) return go(launch_variant<uint32_t, 1024, 4, 1, false>, gstate);
     switch (plan.threads) {
         case 128:

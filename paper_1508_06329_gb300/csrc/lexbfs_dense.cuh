@@ -72,7 +72,9 @@ struct IdTraits<uint32_t> {
 
 template <typename Id>
 struct LexState {
-    CG_ARR(typename IdTraits<Id>::Sz) sz;  // [n]     size | moved-this-step << kShift
+    CG_ARR(typename IdTraits<Id>::Sz) sz;  // [n]     size | moved-this-step << kShift (size only with mvw)
+    CG_ARR(uint32_t) mvw;                  // [(n+1)/2] moved-this-step, two 16-bit counts per word (split layouts 2, 3)
+    CG_ARR(uint16_t) mvh;                  // [n]     the same counts as 16-bit entries (stores)
     CG_ARR(Id) cls;                        // [n]     class of each vertex, kNumbered once visited
     CG_ARR(Id) child;                      // [n]     class receiving a class's pivot neighbours
     CG_ARR(Id) freel;                      // [n]     stack of unused class ids
@@ -121,37 +123,58 @@ __device__ inline LexState<Id> lex_state_carve(unsigned char *base, int n) {
 
 constexpr size_t kLexScalarBytes = (sizeof(LexScalars) + 15) & ~size_t(15);
 
-// Split layout for graphs too large for the whole state in shared memory but
-// within 16-bit ids: the per-vertex class ids and the numbered bitmask (read
-// and written for every moved vertex and by class scans) stay in shared
-// memory; the per-class arrays go to a global workspace.
+// Split layouts for graphs too large for the whole state in shared memory but
+// within 16-bit ids.  Layout 1: the per-vertex class ids and the numbered
+// bitmask (read and written for every moved vertex and by class scans) stay in
+// shared memory, the per-class arrays go to a global workspace.  Layout 2
+// adds the per-class moved counts (16 bits each, two per word for the shared
+// atomics) and layout 3 the children to shared memory, so a moved vertex's
+// count and relabel stay on chip; sizes, the free stack and the class list
+// (touched once per split class) stay global.
+constexpr int kLayoutSplit = 1, kLayoutSplitMv = 2, kLayoutSplitMvChild = 3;
+
 template <typename Id>
-__host__ __device__ inline size_t lex_split_smem_bytes(int n) {
+__host__ __device__ inline size_t lex_split_smem_bytes(int n, int layout = kLayoutSplit) {
     size_t b = ((size_t)n * sizeof(Id) + 15) & ~size_t(15);
-    b += (size_t)((n + 31) / 32) * sizeof(uint32_t);
-    return (b + 15) & ~size_t(15);
+    b += ((size_t)((n + 31) / 32) * sizeof(uint32_t) + 15) & ~size_t(15);
+    if (layout >= kLayoutSplitMv) b += ((size_t)((n + 1) / 2) * sizeof(uint32_t) + 15) & ~size_t(15);
+    if (layout >= kLayoutSplitMvChild) b += ((size_t)n * sizeof(Id) + 15) & ~size_t(15);
+    return b;
 }
 
 template <typename Id>
-__host__ __device__ inline size_t lex_split_global_bytes(int n) {
+__host__ __device__ inline size_t lex_split_global_bytes(int n, int layout = kLayoutSplit) {
     using Sz = typename IdTraits<Id>::Sz;
-    const size_t b = (size_t)n * sizeof(Sz) + (size_t)n * sizeof(Id) * 2 + (size_t)(n + 1) * sizeof(Id) * 2;
+    const size_t child = layout >= kLayoutSplitMvChild ? 0 : 1;
+    const size_t b = (size_t)n * sizeof(Sz) + (size_t)n * sizeof(Id) * (1 + child) + (size_t)(n + 1) * sizeof(Id) * 2;
     return (b + 255) & ~size_t(255);
 }
 
-template <typename Id>
+template <typename Id, int LAYOUT>
 __device__ inline LexState<Id> lex_state_carve_split(unsigned char *smem, unsigned char *gmem, int n) {
     using Sz = typename IdTraits<Id>::Sz;
     LexState<Id> s;
-    s.cls = cg_arr(reinterpret_cast<Id *>(smem), n, kChkCls);
-    s.numbered = cg_arr(reinterpret_cast<uint32_t *>(smem + (((size_t)n * sizeof(Id) + 15) & ~size_t(15))),
-                        (n + 31) / 32, kChkNumbered);
+    unsigned char *q = smem;
+    s.cls = cg_arr(reinterpret_cast<Id *>(q), n, kChkCls);
+    q += ((size_t)n * sizeof(Id) + 15) & ~size_t(15);
+    s.numbered = cg_arr(reinterpret_cast<uint32_t *>(q), (n + 31) / 32, kChkNumbered);
+    q += ((size_t)((n + 31) / 32) * sizeof(uint32_t) + 15) & ~size_t(15);
+    if constexpr (LAYOUT >= kLayoutSplitMv) {
+        s.mvw = cg_arr(reinterpret_cast<uint32_t *>(q), (n + 1) / 2, kChkMoved);
+        s.mvh = cg_arr(reinterpret_cast<uint16_t *>(q), n, kChkMoved);
+        q += ((size_t)((n + 1) / 2) * sizeof(uint32_t) + 15) & ~size_t(15);
+    }
     s.sz = cg_arr(reinterpret_cast<Sz *>(gmem), n, kChkSize);
     Id *p = reinterpret_cast<Id *>(gmem + (size_t)n * sizeof(Sz));
-    s.child = cg_arr(p, n, kChkChild);
-    s.freel = cg_arr(p + n, n, kChkFree);
-    s.cnext = cg_arr(p + 2 * (size_t)n, n + 1, kChkCnext);
-    s.cprev = cg_arr(p + 3 * (size_t)n + 1, n + 1, kChkCprev);
+    if constexpr (LAYOUT >= kLayoutSplitMvChild) {
+        s.child = cg_arr(reinterpret_cast<Id *>(q), n, kChkChild);
+    } else {
+        s.child = cg_arr(p, n, kChkChild);
+        p += n;
+    }
+    s.freel = cg_arr(p, n, kChkFree);
+    s.cnext = cg_arr(p + n, n + 1, kChkCnext);
+    s.cprev = cg_arr(p + 2 * (size_t)n + 1, n + 1, kChkCprev);
     return s;
 }
 
@@ -178,7 +201,7 @@ __device__ __forceinline__ uint32_t row_raw(const uint32_t *__restrict__ rows, i
 // share each row word (thread t takes bit slice t % lpw of word t / lpw +
 // k * T / lpw), which shortens the serial bit loop; lpw grows while T / lpw
 // still covers the row.
-template <typename Id, int T, int WPT, int LPW>
+template <typename Id, int T, int WPT, int LPW, bool SEPMV = false>
 __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n, LexState<Id> st,
                            LexScalars *sc, int32_t *__restrict__ order, int32_t *__restrict__ pos,
                            int32_t *__restrict__ parent, int pmode = kParentMoves,
@@ -208,6 +231,8 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
     }
     for (int k = t; k < n - 1; k += T) st.freel[k] = (Id)(k + 1);
     for (int w = t; w < wn; w += T) st.numbered[w] = 0u;
+    if constexpr (SEPMV)
+        for (int w = t; w < (n + 1) / 2; w += T) st.mvw[w] = 0u;
     if (t == 0) {
         st.sz[0] = (Sz)n;
         st.cnext[HEAD] = 0;
@@ -233,12 +258,21 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
     int par_x = -1;   // p(x) of the current pivot (thread 0, kParentPivots)
     __syncthreads();
 
+    // adds k to class c's moved count and returns the count before (shared-memory atomics)
+    auto moved_add = [&](Id c, unsigned k) -> unsigned {
+        if constexpr (SEPMV) {
+            const unsigned sh = (unsigned)(c & 1) << 4;
+            return (atomicAdd(&st.mvw[c >> 1], k << sh) >> sh) & 0xFFFFu;
+        } else {
+            return (unsigned)(atomicAdd(&st.sz[c], (Sz)k << Tr::kShift) >> Tr::kShift);
+        }
+    };
     auto step = [&](const int i, uint32_t (&row_prev)[WPT], uint32_t (&row_cur)[WPT],
                     uint32_t (&row_nxt)[WPT]) -> bool {
         const int slot = i & 1;
         const Id f = st.cnext[HEAD];
         const Id g = st.cnext[f];
-        const Sz fsz = st.sz[f] & Tr::kMask;  // still counts x
+        const Sz fsz = SEPMV ? st.sz[f] : st.sz[f] & Tr::kMask;  // still counts x
         // uniform shortcuts: when the previous step split no class, every class
         // that moved kept its id and the relabel is a no-op; when f is the only
         // class, every unnumbered neighbour of x is in f and a warp adds its
@@ -298,8 +332,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                     bits &= bits - 1;
                     const int y = (w << 5) + b;
                     const Id c = st.cls[y];
-                    const Sz old = atomicAdd(&st.sz[c], (Sz)1 << Tr::kShift);
-                    if ((old >> Tr::kShift) == 0) am |= bit;
+                    if (moved_add(c, 1u) == 0) am |= bit;
                     if (!f_done && c == f) {
                         atomicMin(&sc->front_min[slot], (unsigned)y);
                         f_done = true;
@@ -320,8 +353,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                 const unsigned total = __reduce_add_sync(0xFFFFFFFFu, (unsigned)__popc(cur));
                 const unsigned lanes = __ballot_sync(0xFFFFFFFFu, cur != 0u);
                 if (lanes && (t & 31) == __ffs(lanes) - 1) {   // the warp's lowest moved vertex
-                    const Sz old = atomicAdd(&st.sz[f], (Sz)total << Tr::kShift);
-                    if ((old >> Tr::kShift) == 0) am = cur & (0u - cur);   // first arrival allocates
+                    if (moved_add(f, total) == 0) am = cur & (0u - cur);   // first arrival allocates
                     atomicMin(&sc->front_min[slot], (unsigned)((w << 5) + __ffs(cur) - 1));
                 }
             }
@@ -367,9 +399,16 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                 const int y = (w << 5) + (__ffs(am) - 1);
                 am &= am - 1;
                 const Id c = st.cls[y];  // class before this step's move (relabel is deferred)
-                const Sz s = st.sz[c];
-                const Sz mv = s >> Tr::kShift;
-                const Sz size = (s & Tr::kMask) - (c == f ? 1 : 0);
+                Sz mv, size;
+                if constexpr (SEPMV) {
+                    mv = (st.mvw[c >> 1] >> ((c & 1) << 4)) & 0xFFFFu;
+                    size = st.sz[c] - (c == f ? 1 : 0);
+                    st.mvh[c] = 0;   // the moved count restarts (the other half of the word is another class's)
+                } else {
+                    const Sz s = st.sz[c];
+                    mv = s >> Tr::kShift;
+                    size = (s & Tr::kMask) - (c == f ? 1 : 0);
+                }
                 if (mv == size) {
                     st.child[c] = c;
                     st.sz[c] = size;

@@ -155,8 +155,8 @@ def test_large_dense_workload_full_size(ctx):
 
 
 def test_wide_ids_beyond_shared_memory(ctx):
-    """n > 16,384 takes the 32-bit-id variant with state in the workspace."""
-    for n, t in ((16385, 2000), (20000, 3000)):
+    """n > 16,384 keeps part of the state in the workspace (the split layouts)."""
+    for n, t in ((16385, 2000), (20000, 3000), (40000, 20000)):
         g = gg.subtree_dense(n, t, n)
         assert_parity(ctx, g)
         h, _ = gg.plant_cycle(g, 6, n)
@@ -249,10 +249,12 @@ def test_argument_errors(ctx):
     assert B.cg_chordal_test_dense(ctx.handle, B.ctypes.byref(bad), res.data_ptr(), None, None) == B.CG_EINVAL
 
 
-@pytest.mark.parametrize("n", [65520, 65521])
+@pytest.mark.parametrize("n", [37920, 37921, 56312, 56313, 65520, 65521])
 def test_variant_size_limits(ctx, n):
-    """The largest graph of the split-state variant (16-bit ids) and the first
-    one of the 32-bit-id variant; sparse graphs keep the oracle fast."""
+    """The largest graph of each split-state layout (16-bit ids: moved counts
+    and children in shared memory up to 37,920 vertices, moved counts up to
+    56,312, neither up to 65,520), the first one of the next, and the first one
+    of the 32-bit-id variant; sparse graphs keep the oracle fast."""
     g = gg.random_tree(n, n)
     assert assert_parity(ctx, g).chordal == 1
     h = g.copy()
