@@ -100,7 +100,8 @@ int cg_context_destroy(cg_context *ctx);
  * LexBFS order of a dense graph (Section 4.2: pick the first vertex of the
  * first class, split every class C into C ∩ N_x placed before C \ N_x;
  * Section 6.1 runs it on the GPU).  One persistent CTA walks all n steps with
- * the partition state in shared memory (n <= 16384) or in the workspace.
+ * the partition state in shared memory (n <= 16384), split between shared
+ * memory and the workspace (n <= 65520) or in the workspace.
  *   g      device graph, n >= 0, n <= 131072
  *   order  device int32[n] (written)
  *   pos    device int32[n] (written) or NULL
@@ -151,7 +152,11 @@ int cg_lexbfs_sweep_csr(cg_context *ctx, const cg_csr *g, int32_t kind, const in
 int cg_peo_check_dense(cg_context *ctx, const cg_dense *g, const int32_t *order, int32_t *parent,
                        cg_result *res, cudaStream_t stream);
 
-/* The whole test on one dense graph: LexBFS, then the check.
+/* The whole test on one dense graph: LexBFS, then the check (Sections 4.2,
+ * 5.2-5.3, 6.1-6.2).  The search also records every vertex's parent p(v) and
+ * the earlier-than masks; the check stages runs of rows in shared memory when
+ * n <= 49152 and the rows are 16-byte aligned with words_per_row a multiple
+ * of 4, else it reads them from global memory.
  *   res    device cg_result (written)
  *   order  device int32[n] (written) or NULL */
 int cg_chordal_test_dense(cg_context *ctx, const cg_dense *g, cg_result *res, int32_t *order,

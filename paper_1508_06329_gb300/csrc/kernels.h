@@ -13,8 +13,8 @@ struct LexPlan {
     int threads;        // CTA size
     bool rows_smem;     // adjacency copied into shared memory
     bool wide_ids;      // 32-bit ids, state in a global workspace
-    int split_state;    // 16-bit ids, class ids in shared memory, class arrays in a global workspace:
-                        // 0 no, else the split layout 1..3 (more per-class arrays in shared memory)
+    int split_state;    // 16-bit ids, class ids in shared memory, class arrays partly in a global
+                        // workspace: 0 no, else the split layout 2, 3 or 5 (lexbfs_dense.cuh)
     size_t smem_bytes;  // dynamic shared memory per CTA
     size_t gstate_bytes;// global state bytes per CTA (0: none)
     int n_max;          // the largest graph the plan was made for

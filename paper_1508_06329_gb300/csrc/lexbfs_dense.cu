@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(T) lexbfs_dense_kernel(const DenseDesc *__rest
         }
         // the per-class last pivot: in shared memory when it fits beside the state
         int32_t *cp = cpar ? (cpar_smem ? reinterpret_cast<int32_t *>(p) : cpar + d.vbase) : nullptr;
-        lexbfs_cta<Id, T, WPT, LPW, (SPLIT >= kLayoutSplitMv)>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr,
+        lexbfs_cta<Id, T, WPT, LPW, layout_mv(SPLIT) ? 1 : layout_arr(SPLIT) ? 2 : 0>(rows, stride, n, st, sc, order + d.obase, pos ? pos + d.vbase : nullptr,
                                     parent ? parent + d.vbase : nullptr, pmode, emask ? emask + d.ebase : nullptr,
                                     cp);
         __syncthreads();
@@ -138,8 +138,8 @@ int lexbfs_dense_plan(int n_max, int threads_override, LexPlan *plan) {
         p.rows_smem = false;
         p.threads = 1024;
         // as much of the per-class state in shared memory as fits
-        p.split_state = kLayoutSplit;
-        for (int l = kLayoutSplitMvChild; l > kLayoutSplit; --l)
+        p.split_state = kLayoutSplitArr;
+        for (int l : {kLayoutSplitMvChild, kLayoutSplitMv})
             if (kLexScalarBytes + lex_split_smem_bytes<uint16_t>(n, l) <= kSmemLimit) {
                 p.split_state = l;
                 break;
@@ -175,7 +175,7 @@ int lexbfs_dense_launch(const LexPlan &plan, const DenseDesc *descs, DenseDesc s
     if (plan.split_state == kLayoutSplitMvChild)
         return go(launch_variant<uint16_t, 1024, 2, 1, false, kLayoutSplitMvChild>, gstate);
     if (plan.split_state == kLayoutSplitMv) return go(launch_variant<uint16_t, 1024, 2, 1, false, kLayoutSplitMv>, gstate);
-    if (plan.split_state) return go(launch_variant<uint16_t, 1024, 2, 1, false, kLayoutSplit>, gstate);
+    if (plan.split_state) return go(launch_variant<uint16_t, 1024, 2, 1, false, kLayoutSplitArr>, gstate);
     if (plan.wide_ids) return go(launch_variant<uint32_t, 1024, 4, 1, false>, gstate);
     switch (plan.threads) {
         case 128:

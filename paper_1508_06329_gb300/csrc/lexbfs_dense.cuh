@@ -75,6 +75,7 @@ struct LexState {
     CG_ARR(typename IdTraits<Id>::Sz) sz;  // [n]     size | moved-this-step << kShift (size only with mvw)
     CG_ARR(uint32_t) mvw;                  // [(n+1)/2] moved-this-step, two 16-bit counts per word (split layouts 2, 3)
     CG_ARR(uint16_t) mvh;                  // [n]     the same counts as 16-bit entries (stores)
+    CG_ARR(uint32_t) arrived;              // [ceil(n/32)] class c's bit: a member moved this step (layout 5)
     CG_ARR(Id) cls;                        // [n]     class of each vertex, kNumbered once visited
     CG_ARR(Id) child;                      // [n]     class receiving a class's pivot neighbours
     CG_ARR(Id) freel;                      // [n]     stack of unused class ids
@@ -124,28 +125,40 @@ __device__ inline LexState<Id> lex_state_carve(unsigned char *base, int n) {
 constexpr size_t kLexScalarBytes = (sizeof(LexScalars) + 15) & ~size_t(15);
 
 // Split layouts for graphs too large for the whole state in shared memory but
-// within 16-bit ids.  Layout 1: the per-vertex class ids and the numbered
-// bitmask (read and written for every moved vertex and by class scans) stay in
-// shared memory, the per-class arrays go to a global workspace.  Layout 2
-// adds the per-class moved counts (16 bits each, two per word for the shared
-// atomics) and layout 3 the children to shared memory, so a moved vertex's
-// count and relabel stay on chip; sizes, the free stack and the class list
-// (touched once per split class) stay global.
-constexpr int kLayoutSplit = 1, kLayoutSplitMv = 2, kLayoutSplitMvChild = 3;
+// within 16-bit ids.  The per-vertex class ids and the numbered bitmask (read
+// and written for every moved vertex and by class scans) always stay in
+// shared memory; of the per-class state, what a moved vertex touches goes
+// there too as far as it fits, the rest (sizes, the free stack and the class
+// list, touched once per split class) to a global workspace:
+//   layout 3 (n <= 37,920): the moved counts (16 bits each, two per word for
+//     the shared atomics) and the children;
+//   layout 2 (n <= 56,312): the moved counts;
+//   layout 5 (n <= 65,520): one "arrived" bit per class (the first moved
+//     member's atomicOr elects the class's allocator); the counts are added
+//     to the packed global size words without a return value.
+// (Arrival bits with the children in shared memory and the counts in global
+// memory, measured on GB300 for 37,921..54,656 vertices, matched layout 2 on
+// a sparse graph but were ~1.4x slower per step on a dense one, whose moved
+// vertices pile onto few global count words.)
+constexpr int kLayoutSplitMv = 2, kLayoutSplitMvChild = 3, kLayoutSplitArr = 5;
+__host__ __device__ constexpr bool layout_mv(int l) { return l == kLayoutSplitMv || l == kLayoutSplitMvChild; }
+__host__ __device__ constexpr bool layout_child(int l) { return l == kLayoutSplitMvChild; }
+__host__ __device__ constexpr bool layout_arr(int l) { return l == kLayoutSplitArr; }
 
 template <typename Id>
-__host__ __device__ inline size_t lex_split_smem_bytes(int n, int layout = kLayoutSplit) {
+__host__ __device__ inline size_t lex_split_smem_bytes(int n, int layout) {
     size_t b = ((size_t)n * sizeof(Id) + 15) & ~size_t(15);
     b += ((size_t)((n + 31) / 32) * sizeof(uint32_t) + 15) & ~size_t(15);
-    if (layout >= kLayoutSplitMv) b += ((size_t)((n + 1) / 2) * sizeof(uint32_t) + 15) & ~size_t(15);
-    if (layout >= kLayoutSplitMvChild) b += ((size_t)n * sizeof(Id) + 15) & ~size_t(15);
+    if (layout_mv(layout)) b += ((size_t)((n + 1) / 2) * sizeof(uint32_t) + 15) & ~size_t(15);
+    if (layout_arr(layout)) b += ((size_t)((n + 31) / 32) * sizeof(uint32_t) + 15) & ~size_t(15);
+    if (layout_child(layout)) b += ((size_t)n * sizeof(Id) + 15) & ~size_t(15);
     return b;
 }
 
 template <typename Id>
-__host__ __device__ inline size_t lex_split_global_bytes(int n, int layout = kLayoutSplit) {
+__host__ __device__ inline size_t lex_split_global_bytes(int n, int layout) {
     using Sz = typename IdTraits<Id>::Sz;
-    const size_t child = layout >= kLayoutSplitMvChild ? 0 : 1;
+    const size_t child = layout_child(layout) ? 0 : 1;
     const size_t b = (size_t)n * sizeof(Sz) + (size_t)n * sizeof(Id) * (1 + child) + (size_t)(n + 1) * sizeof(Id) * 2;
     return (b + 255) & ~size_t(255);
 }
@@ -159,14 +172,18 @@ __device__ inline LexState<Id> lex_state_carve_split(unsigned char *smem, unsign
     q += ((size_t)n * sizeof(Id) + 15) & ~size_t(15);
     s.numbered = cg_arr(reinterpret_cast<uint32_t *>(q), (n + 31) / 32, kChkNumbered);
     q += ((size_t)((n + 31) / 32) * sizeof(uint32_t) + 15) & ~size_t(15);
-    if constexpr (LAYOUT >= kLayoutSplitMv) {
+    if constexpr (layout_mv(LAYOUT)) {
         s.mvw = cg_arr(reinterpret_cast<uint32_t *>(q), (n + 1) / 2, kChkMoved);
         s.mvh = cg_arr(reinterpret_cast<uint16_t *>(q), n, kChkMoved);
         q += ((size_t)((n + 1) / 2) * sizeof(uint32_t) + 15) & ~size_t(15);
     }
+    if constexpr (layout_arr(LAYOUT)) {
+        s.arrived = cg_arr(reinterpret_cast<uint32_t *>(q), (n + 31) / 32, kChkMoved);
+        q += ((size_t)((n + 31) / 32) * sizeof(uint32_t) + 15) & ~size_t(15);
+    }
     s.sz = cg_arr(reinterpret_cast<Sz *>(gmem), n, kChkSize);
     Id *p = reinterpret_cast<Id *>(gmem + (size_t)n * sizeof(Sz));
-    if constexpr (LAYOUT >= kLayoutSplitMvChild) {
+    if constexpr (layout_child(LAYOUT)) {
         s.child = cg_arr(reinterpret_cast<Id *>(q), n, kChkChild);
     } else {
         s.child = cg_arr(p, n, kChkChild);
@@ -201,7 +218,10 @@ __device__ __forceinline__ uint32_t row_raw(const uint32_t *__restrict__ rows, i
 // share each row word (thread t takes bit slice t % lpw of word t / lpw +
 // k * T / lpw), which shortens the serial bit loop; lpw grows while T / lpw
 // still covers the row.
-template <typename Id, int T, int WPT, int LPW, bool SEPMV = false>
+// MV: where the moved counts live: 0 in the packed size words, 1 in the
+// 16-bit counts of st.mvw (split layouts 2, 3), 2 in the packed size words
+// with the allocator elected by st.arrived (split layout 5).
+template <typename Id, int T, int WPT, int LPW, int MV = 0>
 __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n, LexState<Id> st,
                            LexScalars *sc, int32_t *__restrict__ order, int32_t *__restrict__ pos,
                            int32_t *__restrict__ parent, int pmode = kParentMoves,
@@ -231,8 +251,10 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
     }
     for (int k = t; k < n - 1; k += T) st.freel[k] = (Id)(k + 1);
     for (int w = t; w < wn; w += T) st.numbered[w] = 0u;
-    if constexpr (SEPMV)
+    if constexpr (MV == 1)
         for (int w = t; w < (n + 1) / 2; w += T) st.mvw[w] = 0u;
+    if constexpr (MV == 2)
+        for (int w = t; w < (n + 31) / 32; w += T) st.arrived[w] = 0u;
     if (t == 0) {
         st.sz[0] = (Sz)n;
         st.cnext[HEAD] = 0;
@@ -258,13 +280,18 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
     int par_x = -1;   // p(x) of the current pivot (thread 0, kParentPivots)
     __syncthreads();
 
-    // adds k to class c's moved count and returns the count before (shared-memory atomics)
-    auto moved_add = [&](Id c, unsigned k) -> unsigned {
-        if constexpr (SEPMV) {
+    // adds k to class c's moved count; true for the first arrival of the step
+    // (that thread allocates for the class)
+    auto moved_add = [&](Id c, unsigned k) -> bool {
+        if constexpr (MV == 1) {
             const unsigned sh = (unsigned)(c & 1) << 4;
-            return (atomicAdd(&st.mvw[c >> 1], k << sh) >> sh) & 0xFFFFu;
+            return ((atomicAdd(&st.mvw[c >> 1], k << sh) >> sh) & 0xFFFFu) == 0u;
+        } else if constexpr (MV == 2) {
+            atomicAdd(&st.sz[c], (Sz)k << Tr::kShift);   // no return value: the chain does not wait for it
+            const uint32_t bit = 1u << (c & 31);
+            return (atomicOr(&st.arrived[c >> 5], bit) & bit) == 0u;
         } else {
-            return (unsigned)(atomicAdd(&st.sz[c], (Sz)k << Tr::kShift) >> Tr::kShift);
+            return (atomicAdd(&st.sz[c], (Sz)k << Tr::kShift) >> Tr::kShift) == 0;
         }
     };
     auto step = [&](const int i, uint32_t (&row_prev)[WPT], uint32_t (&row_cur)[WPT],
@@ -272,7 +299,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
         const int slot = i & 1;
         const Id f = st.cnext[HEAD];
         const Id g = st.cnext[f];
-        const Sz fsz = SEPMV ? st.sz[f] : st.sz[f] & Tr::kMask;  // still counts x
+        const Sz fsz = MV == 1 ? st.sz[f] : st.sz[f] & Tr::kMask;  // still counts x
         // uniform shortcuts: when the previous step split no class, every class
         // that moved kept its id and the relabel is a no-op; when f is the only
         // class, every unnumbered neighbour of x is in f and a warp adds its
@@ -332,7 +359,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                     bits &= bits - 1;
                     const int y = (w << 5) + b;
                     const Id c = st.cls[y];
-                    if (moved_add(c, 1u) == 0) am |= bit;
+                    if (moved_add(c, 1u)) am |= bit;
                     if (!f_done && c == f) {
                         atomicMin(&sc->front_min[slot], (unsigned)y);
                         f_done = true;
@@ -353,7 +380,7 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                 const unsigned total = __reduce_add_sync(0xFFFFFFFFu, (unsigned)__popc(cur));
                 const unsigned lanes = __ballot_sync(0xFFFFFFFFu, cur != 0u);
                 if (lanes && (t & 31) == __ffs(lanes) - 1) {   // the warp's lowest moved vertex
-                    if (moved_add(f, total) == 0) am = cur & (0u - cur);   // first arrival allocates
+                    if (moved_add(f, total)) am = cur & (0u - cur);   // first arrival allocates
                     atomicMin(&sc->front_min[slot], (unsigned)((w << 5) + __ffs(cur) - 1));
                 }
             }
@@ -400,11 +427,12 @@ __device__ void lexbfs_cta(const uint32_t *__restrict__ rows, int stride, int n,
                 am &= am - 1;
                 const Id c = st.cls[y];  // class before this step's move (relabel is deferred)
                 Sz mv, size;
-                if constexpr (SEPMV) {
+                if constexpr (MV == 1) {
                     mv = (st.mvw[c >> 1] >> ((c & 1) << 4)) & 0xFFFFu;
                     size = st.sz[c] - (c == f ? 1 : 0);
                     st.mvh[c] = 0;   // the moved count restarts (the other half of the word is another class's)
                 } else {
+                    if constexpr (MV == 2) atomicAnd(&st.arrived[c >> 5], ~(1u << (c & 31)));
                     const Sz s = st.sz[c];
                     mv = s >> Tr::kShift;
                     size = (s & Tr::kMask) - (c == f ? 1 : 0);

@@ -253,8 +253,8 @@ def test_argument_errors(ctx):
 def test_variant_size_limits(ctx, n):
     """The largest graph of each split-state layout (16-bit ids: moved counts
     and children in shared memory up to 37,920 vertices, moved counts up to
-    56,312, neither up to 65,520), the first one of the next, and the first one
-    of the 32-bit-id variant; sparse graphs keep the oracle fast."""
+    56,312, arrival bits up to 65,520), the first one of the next, and the
+    first one of the 32-bit-id variant; sparse graphs keep the oracle fast."""
     g = gg.random_tree(n, n)
     assert assert_parity(ctx, g).chordal == 1
     h = g.copy()
