@@ -139,7 +139,7 @@ int launch_fused(const FusedPlan &plan, const DenseDesc *descs, int count, int c
 
 }  // namespace
 
-int fused_dense_plan(int n_max, int threads, FusedPlan *plan) {
+int fused_dense_plan(int n_max, int threads, FusedPlan *plan, bool rows_smem_allowed) {
     if (n_max < 0 || n_max > kFusedMaxN)
         return set_error(CG_EINVAL, "fused batch path supports n <= %d (got %d)", kFusedMaxN, n_max);
     const int n = std::max(n_max, 1);
@@ -147,7 +147,7 @@ int fused_dense_plan(int n_max, int threads, FusedPlan *plan) {
     FusedPlan p{};
     const size_t state = lex_state_bytes<uint16_t>(n);
     const size_t rows = (size_t)n * wn * 4;
-    p.rows_smem = kLexScalarBytes + state + rows <= kFusedSmemLimit;
+    p.rows_smem = rows_smem_allowed && kLexScalarBytes + state + rows <= kFusedSmemLimit;
     if (threads == 0) threads = n <= 256 ? 64 : (n <= 1024 ? 128 : 256);
     if (threads != 64 && threads != 128 && threads != 256 && threads != 512)
         return set_error(CG_EINVAL, "fused batch path: unsupported CTA size %d", threads);

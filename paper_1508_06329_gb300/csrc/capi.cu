@@ -243,6 +243,16 @@ int make_layout(cg_context *ctx, const cg_dense *graphs, int32_t count, const in
         const int cnt = B.end - B.begin;
         if (b < 9) {
             if ((rc = fused_dense_plan(B.nmax, ctx->tuned_threads[b], &B.fplan))) return rc;
+            if (B.fplan.rows_smem) {
+                // rows in shared memory make a step faster but can leave one CTA per SM;
+                // with more graphs than that wave holds, rows read from L2 (a step
+                // ~1.3x slower) and more CTAs per SM take fewer waves
+                FusedPlan pg;
+                if ((rc = fused_dense_plan(B.nmax, ctx->tuned_threads[b], &pg, false))) return rc;
+                const int64_t ws = ceil_div(cnt, (int64_t)ctx->num_sms * fused_ctas_per_sm(B.fplan));
+                const int64_t wg = ceil_div(cnt, (int64_t)ctx->num_sms * fused_ctas_per_sm(pg));
+                if (wg * 13 < ws * 10) B.fplan = pg;
+            }
             B.ctas = std::min(cnt, ctx->num_sms * fused_ctas_per_sm(B.fplan));
         } else {
             if ((rc = lexbfs_dense_plan(B.nmax, ctx->cfg.threads_override, &B.lplan))) return rc;

@@ -105,8 +105,9 @@ struct FusedPlan {
     bool rows_smem;
     size_t smem_bytes;
 };
-// threads = 0 picks by size; otherwise 64, 128, 256 or 512.
-int fused_dense_plan(int n_max, int threads, FusedPlan *plan);
+// threads = 0 picks by size; otherwise 64, 128, 256 or 512.  The rows are
+// copied to shared memory when they fit and rows_smem_allowed.
+int fused_dense_plan(int n_max, int threads, FusedPlan *plan, bool rows_smem_allowed = true);
 int fused_dense_launch(const FusedPlan &plan, const DenseDesc *descs, int count, int ctas, int32_t *order,
                        int32_t *pos, int32_t *parent, cg_result *res, int *work_counter, cudaStream_t stream);
 int fused_ctas_per_sm(const FusedPlan &plan);
