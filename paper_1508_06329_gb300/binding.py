@@ -320,27 +320,39 @@ def chordal_test_batch(ctx: Context, graphs, res, orders=None, order_offsets=Non
                                  offs if offs is not None else None, _stream(stream)))
 
 
+class HostBatch:
+    """The cg_dense descriptors of a list of host graphs, built once: repeated
+    calls on the same host buffers (whose contents may change between calls)
+    skip the per-graph marshalling.  graphs: list of (rows, n) with rows a CPU
+    tensor or ndarray of 32-bit words [n, words] (pinned preferred)."""
+
+    def __init__(self, graphs):
+        import numpy as np
+        self.count = len(graphs)
+        self.arr = (cg_dense * max(self.count, 1))()
+        self._keep = []   # the arrays whose addresses the descriptors hold
+        for k, (rows, n) in enumerate(graphs):
+            if hasattr(rows, "data_ptr"):
+                ptr, words = int(rows.data_ptr()), (int(rows.shape[1]) if rows.dim() == 2 else 0)
+                self._keep.append(rows)
+            else:
+                a = np.ascontiguousarray(rows)
+                self._keep.append(a)
+                ptr, words = a.ctypes.data, (a.shape[1] if a.ndim == 2 else 0)
+            self.arr[k] = cg_dense(n, words, ptr if n > 0 else 0)
+
+
 def chordal_test_batch_host(ctx: Context, graphs, host_res, host_orders=None, stream=None):
-    """graphs: list of (rows, n) with rows a CPU tensor or ndarray of 32-bit words [n, words] (pinned
-    preferred); host_res: CPU int32 tensor/ndarray [count, 4]; host_orders: CPU int32 [sum n] or None."""
-    import numpy as np
-    count = len(graphs)
-    arr = (cg_dense * max(count, 1))()
-    keep = []
-    for k, (rows, n) in enumerate(graphs):
-        if hasattr(rows, "data_ptr"):
-            ptr, words = int(rows.data_ptr()), (int(rows.shape[1]) if rows.dim() == 2 else 0)
-        else:
-            a = np.ascontiguousarray(rows)
-            keep.append(a)
-            ptr, words = a.ctypes.data, (a.shape[1] if a.ndim == 2 else 0)
-        arr[k] = cg_dense(n, words, ptr if n > 0 else 0)
+    """graphs: a HostBatch, or a list of (rows, n) as HostBatch takes; host_res: CPU int32
+    tensor/ndarray [count, 4]; host_orders: CPU int32 [sum n] or None."""
+    batch = graphs if isinstance(graphs, HostBatch) else HostBatch(graphs)
 
     def hptr(x):
         if x is None:
             return None
         return int(x.data_ptr()) if hasattr(x, "data_ptr") else x.ctypes.data
-    _check(cg_chordal_test_batch_host(ctx.handle, arr, count, hptr(host_res), hptr(host_orders), _stream(stream)))
+    _check(cg_chordal_test_batch_host(ctx.handle, batch.arr, batch.count, hptr(host_res), hptr(host_orders),
+                                      _stream(stream)))
 
 
 def csr_desc(row_ptr, col, n: int) -> cg_csr:

@@ -137,3 +137,19 @@ def test_batch_host_entry_full_size_pair(ctx):
     res = np.full((2, 4), -7, dtype=np.int32)
     B.chordal_test_batch_host(ctx, [(g.rows, g.n), (h.rows, h.n)], res)
     assert [tuple(r) for r in res.tolist()] == [oracle.chordal_test(g).witness, oracle.chordal_test(h).witness]
+
+
+def test_batch_host_descriptors_reused_with_new_contents(ctx):
+    """A HostBatch built once over pinned buffers: each call copies the buffers'
+    current contents, so overwriting the rows between calls changes the results."""
+    a = gg.batch_dense(40, seed=41)
+    b = [gg.random_dense(g.n, 0.3, 7 * g.n + k) for k, g in enumerate(a)]   # same sizes, other graphs
+    bufs = [torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32).copy()).pin_memory() for g in a]
+    batch = B.HostBatch([(t, g.n) for t, g in zip(bufs, a)])
+    res = torch.full((len(a), 4), -7, dtype=torch.int32).pin_memory()
+    for graphs in (a, b, a):
+        for t, g in zip(bufs, graphs):
+            t.copy_(torch.from_numpy(np.ascontiguousarray(g.rows).view(np.int32)))
+        B.chordal_test_batch_host(ctx, batch, res)
+        for k, g in enumerate(graphs):
+            assert tuple(res[k].tolist()) == oracle.chordal_test(g).witness, k
