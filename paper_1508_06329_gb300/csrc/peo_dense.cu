@@ -1,5 +1,12 @@
 // peo_dense.cu — perfect-elimination check of dense graphs (Sections 5.2, 6.2).
 //
+// Three forms of the same test.  The check of the search's own order, with
+// exact parents and the earlier-than masks written by the search, is
+// peo_stage_kernel (rows staged in shared memory; further below) or, for
+// graphs beyond its size or with rows unsuited to 16-byte copies,
+// peo_unit_kernel.  The check of a caller-given order (and of an MCS order)
+// is the general form described here.
+//
 // For every vertex v (one warp per vertex, all graphs of a bucket in one grid):
 //   p(v)  = the neighbour of v with the largest order index below pos(v)
 //           (the paper's preparationLNandP kernel);
